@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-spin-coded checkerboard Metropolis sweep on GB300.
+
+Workload (one step): 1000 sweeps of the L = 32768 lattice (2^30 spins, 32 spins
+per 32-bit word, 128 MiB), hot start from seed 7, T = 2.269185, M and E
+recorded after every sweep, then the FP64 moments.  Metric: spin-flip
+attempts per ns (N = L^2 attempts per sweep).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica lattice (stream_id =
+rank); the units of all ranks are summed over the slowest rank's time.
+
+One JSON line on rank 0:
+  value          device-timed attempts/ns, lattice resident in HBM
+  e2e            the same through the C ABI from host buffers: each step
+                 creates the lattice from a pinned host copy (H2D), sweeps,
+                 reads the M/E samples back (D2H) and destroys it
+  roofline       the dominant kernel (the half-sweep) against the integer-ALU
+                 bound; achieved = 16 int32 ops per attempt / mean launch time
+  cpu_baseline   the oracle on this host's cores on a bounded strip sample of
+                 the same workload (rank 0, N = 1 only)
+The reference arm (--impl reference) times the oracle itself on that sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L = 32768
+T = 2.269185
+SEED = 7
+SWEEPS_PER_STEP = 1000
+WORD_BITS = 32
+METRIC = "spin-flip attempts/ns"
+UNIT = "attempts/ns"
+# canonical integer operations per attempt (Philox 10, counter 0.5, compares and
+# bit insertion 4, bit-sliced logic / mask / XOR 1, popcount reductions 0.5)
+OPS_PER_ATTEMPT = 16
+INT32_LANES_PER_SM = 128
+CONFIG = {
+    "workload": "L=32768 (2^30 spins, u32 words, 128 MiB), hot start seed 7, T=2.269185, "
+                "1000 sweeps per step, M/E every sweep",
+    "L": L, "T": T, "seed": SEED, "sweeps_per_step": SWEEPS_PER_STEP, "word_bits": WORD_BITS,
+    "record_every": 1,
+    "l2": "lattice (128 MiB) read+written twice per sweep; L2 flushed (512 MiB write) between steps",
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------- distributed --
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper part of the distribution
+        loaded = [s for s in sm if s >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- profiles --
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1007_3726_gb300", "csrc", "kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per half-sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "half_sweep_u32_L32768.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernels\.cu sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
+    t = re.search(r"dram bytes per launch:\s*`?([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------- CPU oracle ---
+def oracle_strip_sample(target_s: float, max_sweeps: int | None = None):
+    """Time the oracle on a strip of the workload lattice: rows [0, 256) of the
+    L=32768 hot start, light-cone mode, sweeps until about target_s seconds.
+    Returns (attempts, seconds, sweeps, threads)."""
+    import numpy as np  # noqa: F401
+    import oracle
+
+    oracle.build()
+    rows = 256
+    thr4, thr8 = oracle.thresholds(T)
+    s = oracle.init_hot(L, SEED, 0, 0, rows)
+    attempts = 0
+    sweeps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.run_window(s, L, 0, 1, SEED, 0, thr4, thr8, t0=sweeps)
+        sweeps += 1
+        attempts += (rows - 2) * L  # the two edge rows of the window are held fixed
+        el = time.perf_counter() - t0
+        if el >= target_s or (max_sweeps and sweeps >= max_sweeps):
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return attempts, el, sweeps, threads
+
+
+def cpu_baseline(target_s=12.0):
+    a, el, sw, thr = oracle_strip_sample(target_s)
+    return {"value": a / el / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": "oracle (one int8 per spin, plain C, OpenMP over rows) on rows 0-255 of the "
+                      "L=32768 hot start, %d sweeps in light-cone mode, %.1f s wall, %d threads"
+                      % (sw, el, thr)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_strip_sample(0.0, max_sweeps=1)
+    total_a, total_t, sweeps, threads = 0, 0.0, 0, 1
+    for _ in range(args.steps):
+        a, el, sw, threads = oracle_strip_sample(2.0)
+        total_a += a
+        total_t += el
+        sweeps += sw
+    v = total_a / total_t / 1e9
+    line = {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_t * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8",
+        "data": "synthetic", "config": CONFIG, "impl": "reference",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "each step: oracle on rows 0-255 of the L=32768 hot start "
+                                   "for about 2 s (%d sweeps in total)" % sweeps},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- ours --
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1007_3726_gb300 as P
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    P.load()
+    stream = torch.cuda.Stream(device=dev)
+    N = L * L
+    units_per_step = N * SWEEPS_PER_STEP
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    # ---------------- device-resident timing
+    lat = P.Lattice(L, T, seed=SEED, stream_id=rank, init="hot", word_bits=WORD_BITS, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lat.sweep(SWEEPS_PER_STEP, 1)
+            lat.measure()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)           # evict the lattice from L2 between steps
+            ev[i][0].record(stream)
+            lat.sweep(SWEEPS_PER_STEP, 1)   # 2 half-sweep launches per sweep
+            ev[i][1].record(stream)
+        lat.measure()                       # harvests the samples, FP64 moments on the host
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = max_over_ranks(sum(step_ms) / 1e3)
+    value = units_per_step * args.steps * ws / t_dev / 1e9
+    obs = lat.measure()
+    lat.close()
+    launches = 2 * SWEEPS_PER_STEP * args.steps
+    mean_launch_s = sum(step_ms) / 1e3 / launches
+
+    # ---------------- end to end through the C ABI from host buffers
+    src = P.Lattice(L, T, seed=SEED, stream_id=rank, init="hot", word_bits=WORD_BITS, stream=stream)
+    packed = src.packed()
+    src.close()
+    host = torch.from_numpy(packed).pin_memory()
+    hp = host.numpy()
+    Mh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
+    Eh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
+
+    def e2e_step():
+        lt = P.Lattice(L, T, seed=SEED, stream_id=rank, packed=hp, word_bits=WORD_BITS,
+                       stream=stream)
+        P.ising_sweep(lt.handle, SWEEPS_PER_STEP, 1, Mh, Eh, SWEEPS_PER_STEP)
+        d = lt.measure()
+        lt.close()
+        return d
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e_wall = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e_wall)
+    e2e_value = units_per_step * args.steps * ws / t_e2e / 1e9
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+    peak_tops = sms * INT32_LANES_PER_SM * sm_max_ghz * 1e9 / 1e12
+    achieved_tops = OPS_PER_ATTEMPT * (N / 2) / mean_launch_s / 1e12
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": dict(CONFIG, parallelism="replicas" if ws > 1 else "single"),
+        "roofline": {
+            "bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
+            "frac": achieved_tops / peak_tops, "traffic": traffic,
+            "kernel": "k_half_sweep<uint32_t>",
+            "peak_basis": "%d SMs x %d int32 lanes x %.2f GHz (max SM clock)" % (
+                sms, INT32_LANES_PER_SM, sm_max_ghz),
+            "achieved_basis": "%d ops/attempt x N/2 attempts per launch / mean launch time %.1f us"
+                              % (OPS_PER_ATTEMPT, mean_launch_s * 1e6),
+            "hbm_view": {"bytes_per_launch_algorithmic": N / 8 * 2,
+                         "achieved_gbs": N / 8 * 2 / mean_launch_s / 1e9,
+                         "peak_gbs": peaks.get("hbm_gbs"), "peak_note": "of measured"},
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(packed.nbytes),
+                "d2h_bytes_per_step": int(Mh.nbytes + Eh.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed": wall,
+        "observables_last_step": {"U4": obs["U4"], "mean_abs_m": obs["mean_abs_m"],
+                                  "mean_e": obs["mean_e"], "n_samples": obs["n_samples"]},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

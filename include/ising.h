@@ -1,0 +1,181 @@
+/*
+ * ising.h - C ABI of the GB300 (sm_103a) multi-spin-coded checkerboard
+ * Metropolis sweep of the 2D Ising model, after Block, Virnau, Preis,
+ * "Multi-GPU Accelerated Multi-Spin Monte Carlo Simulations of the 2D Ising
+ * Model" (arXiv:1007.3726).
+ *
+ * Model (Sec. 3, Eq. 1): spins S = +1 / -1 on an L x L square lattice with
+ * periodic boundaries, H = -J sum_<ij> S_i S_j with J = 1 and no field.
+ * Dynamics (Sec. 3): Metropolis, checkerboard order: step A updates the sites
+ * with (x + y) even, then step B the sites with (x + y) odd; a sweep is A then
+ * B.  A move with dE <= 0 is always accepted; dE = 4 or 8 is accepted when the
+ * site's 32-bit Philox4x32-10 draw u satisfies u < floor(2^32 exp(-dE/T))
+ * (Sec. 3 precomputed factors, Eq. 3 with the strict "<").
+ * Storage (Sec. 4 multi-spin coding, Sec. 5.2 "one bit per spin"): rows of
+ * 32- or 64-bit words, bit b of word w of row y is site x = w * bits + b,
+ * a set bit is S = +1.
+ *
+ * Random-number contract (replaces the LCG array of Sec. 5.3): in step p of
+ * sweep t (t counts the lattice's sweeps since creation), the site (x, y) with
+ * (x + y) & 1 == p has index j = y * L/2 + x/2 and takes word (j & 3) of
+ * Philox4x32-10 with counter (g mod 2^32, g >> 32, t, stream_id << 1 | p),
+ * g = j >> 2, and key (seed mod 2^32, seed >> 32).  The hot start gives the
+ * site n = y * L + x the value +1 iff bit (n & 31) of word ((n >> 5) & 3) of
+ * Philox4x32-10 with counter (n >> 7 mod 2^32, n >> 39, 0xFFFFFFFF,
+ * stream_id << 1) is set.  Results are therefore fixed bit for bit by
+ * (L, T, seed, stream_id, initial state, number of sweeps), independent of how
+ * the sweeps are split into calls, of the word width and of the launch shape.
+ *
+ * Observables: M = sum S, E = -sum_(x,y) S(x,y) [S(x+1,y) + S(x,y+1)] (every
+ * bond once) as exact int64 after every recorded sweep; FP64 moments, Binder
+ * cumulant U4 = 1 - <m^4> / (3 <m^2>^2) (Sec. 3, Eq. 2) and susceptibility.
+ *
+ * Conventions for every function:
+ *   - No exception or abort crosses this ABI; each call returns an
+ *     ising_status, and ising_last_error() gives the calling thread's last
+ *     message.
+ *   - A handle must not be used by two host threads at once; distinct handles
+ *     are independent.
+ *   - Host pointers are owned by the caller and only read or written during
+ *     the call.  Device memory of a handle is owned by the handle.
+ *   - Work is queued on the handle's CUDA stream (given at creation; NULL is
+ *     the legacy default stream).  Calls that return host data synchronise
+ *     that stream.
+ *   - A CUDA error makes the handle sticky-failed: every later call on it
+ *     returns ISING_ERR_STATE until ising_destroy.
+ */
+#ifndef ISING_H
+#define ISING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISING_API __attribute__((visibility("default")))
+#else
+#define ISING_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ising_lattice ising_lattice; /* opaque; owned by the caller until ising_destroy */
+
+typedef enum {
+    ISING_OK = 0,
+    ISING_ERR_INVALID = 1, /* bad argument; nothing was changed or allocated */
+    ISING_ERR_OOM = 2,     /* device or pinned host allocation failed */
+    ISING_ERR_CUDA = 3,    /* a CUDA call failed; the handle is now failed */
+    ISING_ERR_TIMEOUT = 4, /* a bounded device wait expired; the handle is now failed */
+    ISING_ERR_STATE = 5    /* the handle failed earlier; only ising_destroy is allowed */
+} ising_status;
+
+typedef enum {
+    ISING_COLD_UP = 0,     /* every spin +1 */
+    ISING_COLD_DOWN = 1,   /* every spin -1 */
+    ISING_HOT = 2,         /* i.i.d. +-1, p = 1/2, from Philox (see above) */
+    ISING_FROM_BUFFER = 3, /* host int8 array of L*L values +1/-1, row-major */
+    ISING_FROM_PACKED = 4  /* host array of packed words in the storage layout above */
+} ising_init;
+
+typedef struct {
+    uint64_t L;             /* linear size; a multiple of 64, 64 <= L <= 2^20 */
+    double T;               /* temperature (k_B = J = 1); finite and > 0 */
+    uint64_t seed;          /* Philox key */
+    uint32_t stream_id;     /* independent chain index under one seed; < 2^31 */
+    ising_init init;        /* initial state */
+    const void *init_data;  /* host data for FROM_BUFFER (int8) / FROM_PACKED (words); else NULL */
+    uint32_t word_bits;     /* 32, 64, or 0 = automatic (64 when L >= 2^16, else 32) */
+} ising_params;
+
+typedef struct {
+    uint64_t sweeps_done;   /* sweeps applied since creation */
+    uint64_t n_samples;     /* samples recorded so far */
+    int64_t M, E;           /* magnetisation and energy of the current state */
+    double mean_m, mean_abs_m, mean_m2, mean_m4; /* m = M / N over all samples */
+    double mean_e, mean_e2;                      /* e = E / N */
+    double U4;              /* 1 - <m^4> / (3 <m^2>^2)   (Sec. 3, Eq. 2) */
+    double chi;             /* N (<m^2> - <|m|>^2) / T */
+    double C;               /* N (<e^2> - <e>^2) / T^2 */
+} ising_obs;
+
+/*
+ * Creates a lattice on the current CUDA device: validates *params, computes
+ * the two thresholds in FP64 on the host (Sec. 3), allocates the packed
+ * lattice (L*L/8 bytes) and its per-sweep accumulators, writes the initial
+ * state and counts its M and E.  cuda_stream is a cudaStream_t (or NULL).
+ * On failure *out is NULL and nothing stays allocated.
+ */
+ISING_API ising_status ising_create(const ising_params *params, void *cuda_stream, ising_lattice **out);
+
+/*
+ * Applies nsweeps sweeps (step A then step B each, Sec. 3; two dependent
+ * launches per sweep, the global synchronisation of Sec. 5.2).  A sample
+ * (M, E) is recorded after every sweep whose global count sweeps_done becomes
+ * a multiple of record_every (0 = record nothing); samples accumulate on the
+ * handle for ising_measure.  If M_out and E_out are not NULL they receive the
+ * samples of this call in order, at most cap of them (ISING_ERR_INVALID when
+ * cap is smaller than the number this call records; nothing runs then), and
+ * the call waits for the GPU.  Otherwise the call returns once the work is
+ * queued.  ISING_ERR_INVALID if sweeps_done + nsweeps would reach 2^32 - 1.
+ */
+ISING_API ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_every,
+                         int64_t *M_out, int64_t *E_out, uint64_t cap);
+
+/*
+ * Waits for the handle's stream and fills *out: counters, the current M and E,
+ * and FP64 moments of all samples recorded so far, summed in sample order on
+ * the host.  With no samples the moments are 0.
+ */
+ISING_API ising_status ising_measure(ising_lattice *h, ising_obs *out);
+
+/* Releases everything the handle owns.  NULL is a no-op; always returns ISING_OK
+ * unless freeing reported a CUDA error. */
+ISING_API ising_status ising_destroy(ising_lattice *h);
+
+/* ---- helpers (tests, checkpointing, serving) ---------------------------- */
+
+/* Copies rows [row0, row0 + nrows) of the current state to out (host, nrows*L
+ * int8 values +1/-1, row-major).  Waits for the GPU. */
+ISING_API ising_status ising_get_spins(ising_lattice *h, uint64_t row0, uint64_t nrows, int8_t *out);
+
+/* Copies the packed words of the whole lattice to out (host, L * L/8 bytes, the
+ * storage layout above with the handle's word width).  Waits for the GPU. */
+ISING_API ising_status ising_get_packed(ising_lattice *h, void *out, size_t bytes);
+
+/* Full popcount recount of the current state on the GPU (independent of the
+ * values fused into the sweep).  Waits for the GPU. */
+ISING_API ising_status ising_recount(ising_lattice *h, int64_t *M, int64_t *E);
+
+/* Word width (32 or 64), L, and sweeps done of a handle. */
+ISING_API ising_status ising_info(const ising_lattice *h, uint32_t *word_bits, uint64_t *L,
+                        uint64_t *sweeps_done);
+
+/* Device address of the packed lattice and its size in bytes (owned by the handle). */
+ISING_API ising_status ising_device_spins(const ising_lattice *h, void **dptr, size_t *bytes);
+
+/* The two Metropolis thresholds floor(2^32 exp(-4/T)) and floor(2^32 exp(-8/T))
+ * in FP64 (Sec. 3); ISING_ERR_INVALID for T not finite and positive.  A T whose
+ * factor rounds to 1.0 gives 2^32 - 1. */
+ISING_API ising_status ising_thresholds(double T, uint32_t *thr4, uint32_t *thr8);
+
+/* Thread-local text of the last failure on this thread ("" if none). */
+ISING_API const char *ising_last_error(void);
+
+/*
+ * Optional device allocator for every later allocation of the library (for
+ * example PyTorch's caching allocator).  alloc(bytes, stream, ctx) returns a
+ * device pointer or NULL (reported as ISING_ERR_OOM); release(ptr, stream,
+ * ctx) frees it.  Passing NULL functions restores cudaMalloc / cudaFree.  Must
+ * not be changed while handles created under another allocator are alive.
+ */
+typedef void *(*ising_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx);
+typedef void (*ising_free_fn)(void *ptr, void *cuda_stream, void *ctx);
+ISING_API ising_status ising_set_allocator(ising_alloc_fn alloc, ising_free_fn release, void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_H */

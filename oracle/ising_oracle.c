@@ -118,6 +118,9 @@ void orc_init_hot(int8_t *s, uint64_t L, uint64_t row0, uint64_t nrows,
                   uint64_t seed, uint32_t stream_id)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (nrows * L >= (1u << 18))
+#endif
     for (uint64_t r = 0; r < nrows; ++r) {
         uint64_t y = (row0 + r) % L;
         for (uint64_t x = 0; x < L; ++x) {

@@ -1,0 +1,288 @@
+"""GB300 (sm_103a) multi-spin-coded checkerboard Metropolis sweep of the 2D Ising
+model (after arXiv:1007.3726), behind the C ABI of ``include/ising.h``.
+
+This module is argument marshalling only: every step of the sweep runs in the
+CUDA kernels of ``libising.so`` (built in-tree by ``paper_1007_3726_gb300._build``).
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+
+Raw entry points carry the C names (``ising_create``, ``ising_sweep``,
+``ising_measure``, ``ising_destroy``, ...); ``Lattice`` wraps one handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB_PATH, build  # noqa: F401
+
+__all__ = [
+    "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
+    "ising_measure", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
+    "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
+    "ising_device_spins", "IsingParams", "IsingObs", "INIT_MODES", "STATUS_NAMES",
+]
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
+STATUS_NAMES = {0: "ISING_OK", 1: "ISING_ERR_INVALID", 2: "ISING_ERR_OOM", 3: "ISING_ERR_CUDA",
+                4: "ISING_ERR_TIMEOUT", 5: "ISING_ERR_STATE"}
+INIT_MODES = {"cold_up": 0, "cold": 0, "cold_down": 1, "hot": 2, "buffer": 3, "packed": 4}
+
+
+class IsingError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class IsingParams(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint64), ("T", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("stream_id", ctypes.c_uint32), ("init", ctypes.c_int),
+                ("init_data", ctypes.c_void_p), ("word_bits", ctypes.c_uint32)]
+
+
+class IsingObs(ctypes.Structure):
+    _fields_ = [("sweeps_done", ctypes.c_uint64), ("n_samples", ctypes.c_uint64),
+                ("M", ctypes.c_int64), ("E", ctypes.c_int64),
+                ("mean_m", ctypes.c_double), ("mean_abs_m", ctypes.c_double),
+                ("mean_m2", ctypes.c_double), ("mean_m4", ctypes.c_double),
+                ("mean_e", ctypes.c_double), ("mean_e2", ctypes.c_double),
+                ("U4", ctypes.c_double), ("chi", ctypes.c_double), ("C", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vpp = ctypes.POINTER(ctypes.c_void_p)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+
+
+def load(path: str | None = None):
+    """Load libising.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError("libising.so is not built (%s); run paper_1007_3726_gb300.build()" % path)
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    sig = {
+        "ising_create": ([ctypes.POINTER(IsingParams), ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
+        "ising_sweep": ([H, ctypes.c_uint64, ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64], ctypes.c_int),
+        "ising_measure": ([H, ctypes.POINTER(IsingObs)], ctypes.c_int),
+        "ising_destroy": ([H], ctypes.c_int),
+        "ising_get_spins": ([H, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
+        "ising_get_packed": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+        "ising_recount": ([H, _i64p, _i64p], ctypes.c_int),
+        "ising_info": ([H, _u32p, _u64p, _u64p], ctypes.c_int),
+        "ising_device_spins": ([H, _vpp, _szp], ctypes.c_int),
+        "ising_thresholds": ([ctypes.c_double, _u32p, _u32p], ctypes.c_int),
+        "ising_last_error": ([], ctypes.c_char_p),
+        "ising_set_allocator": ([ALLOC_FN, FREE_FN, ctypes.c_void_p], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise IsingError(status, ising_last_error())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream / ExternalStream
+
+
+# ------------------------------------------------------------- raw C names --
+def ising_last_error() -> str:
+    return load().ising_last_error().decode()
+
+
+def ising_thresholds(T: float) -> tuple[int, int]:
+    a, b = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().ising_thresholds(float(T), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+thresholds = ising_thresholds
+
+
+def ising_create(params: IsingParams, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().ising_create(ctypes.byref(params), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def ising_sweep(h, nsweeps: int, record_every: int = 0, M_out=None, E_out=None, cap: int = 0):
+    mp = M_out.ctypes.data_as(_i64p) if M_out is not None else None
+    ep = E_out.ctypes.data_as(_i64p) if E_out is not None else None
+    _check(load().ising_sweep(h, nsweeps, record_every, mp, ep, cap))
+
+
+def ising_measure(h) -> dict:
+    o = IsingObs()
+    _check(load().ising_measure(h, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def ising_destroy(h):
+    _check(load().ising_destroy(h))
+
+
+def ising_get_spins(h, row0: int, nrows: int, out: np.ndarray):
+    assert out.dtype == np.int8 and out.flags.c_contiguous
+    _check(load().ising_get_spins(h, row0, nrows, out.ctypes.data))
+
+
+def ising_get_packed(h, out: np.ndarray):
+    assert out.flags.c_contiguous
+    _check(load().ising_get_packed(h, out.ctypes.data, out.nbytes))
+
+
+def ising_recount(h) -> tuple[int, int]:
+    M, E = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().ising_recount(h, ctypes.byref(M), ctypes.byref(E)))
+    return M.value, E.value
+
+
+def ising_info(h) -> tuple[int, int, int]:
+    wb, L, sd = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().ising_info(h, ctypes.byref(wb), ctypes.byref(L), ctypes.byref(sd)))
+    return wb.value, L.value, sd.value
+
+
+def ising_device_spins(h) -> tuple[int, int]:
+    p, n = ctypes.c_void_p(), ctypes.c_size_t()
+    _check(load().ising_device_spins(h, ctypes.byref(p), ctypes.byref(n)))
+    return p.value, n.value
+
+
+_alloc_keepalive = []
+
+
+def ising_set_allocator(alloc=None, release=None, ctx=None):
+    """Install Python callables alloc(bytes, stream) -> int and release(ptr, stream)
+    as the library's device allocator (None restores cudaMalloc)."""
+    if alloc is None:
+        _alloc_keepalive.clear()
+        _check(load().ising_set_allocator(ctypes.cast(None, ALLOC_FN), ctypes.cast(None, FREE_FN), None))
+        return
+    a = ALLOC_FN(lambda n, s, c: alloc(n, s) or None)
+    f = FREE_FN(lambda p, s, c: release(p, s))
+    _alloc_keepalive[:] = [a, f]
+    _check(load().ising_set_allocator(a, f, ctx))
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    import torch
+
+    def alloc(n, s):
+        try:
+            return torch.cuda.caching_allocator_alloc(n, stream=s or 0)
+        except RuntimeError:
+            return None
+
+    def release(p, s):
+        torch.cuda.caching_allocator_delete(p)
+
+    ising_set_allocator(alloc, release)
+
+
+# ------------------------------------------------------------------ Lattice --
+class Lattice:
+    """One simulated lattice (a handle of the C ABI)."""
+
+    def __init__(self, L: int, T: float, seed: int = 0, stream_id: int = 0, init: str = "hot",
+                 spins: np.ndarray | None = None, packed: np.ndarray | None = None,
+                 word_bits: int = 0, stream=None):
+        self._h = None
+        data = None
+        if spins is not None:
+            init = "buffer"
+            data = np.ascontiguousarray(spins, dtype=np.int8)
+            assert data.size == L * L
+        elif packed is not None:
+            init = "packed"
+            data = np.ascontiguousarray(packed)
+        self._keep = data
+        p = IsingParams(L=L, T=T, seed=seed, stream_id=stream_id, init=INIT_MODES[init],
+                        init_data=data.ctypes.data if data is not None else None,
+                        word_bits=word_bits)
+        self._h = ising_create(p, stream)
+        self._keep = None
+        self.L, self.T, self.seed, self.stream_id = L, T, seed, stream_id
+        self.word_bits = ising_info(self._h)[0]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sweep(self, nsweeps: int, record_every: int = 0, collect: bool = False):
+        """Run sweeps; with collect=True return this call's (M, E) samples."""
+        if not collect:
+            ising_sweep(self._h, nsweeps, record_every)
+            return None
+        _, _, done = ising_info(self._h)
+        n = (done + nsweeps) // record_every - done // record_every if record_every else 0
+        M = np.zeros(max(n, 1), dtype=np.int64)
+        E = np.zeros(max(n, 1), dtype=np.int64)
+        ising_sweep(self._h, nsweeps, record_every, M, E, n)
+        return M[:n], E[:n]
+
+    def measure(self) -> dict:
+        return ising_measure(self._h)
+
+    def spins(self, row0: int = 0, nrows: int | None = None) -> np.ndarray:
+        nrows = self.L if nrows is None else nrows
+        out = np.empty((nrows, self.L), dtype=np.int8)
+        ising_get_spins(self._h, row0, nrows, out)
+        return out
+
+    def packed(self) -> np.ndarray:
+        dt = np.uint64 if self.word_bits == 64 else np.uint32
+        out = np.empty((self.L, self.L // self.word_bits), dtype=dt)
+        ising_get_packed(self._h, out)
+        return out
+
+    def recount(self) -> tuple[int, int]:
+        return ising_recount(self._h)
+
+    @property
+    def sweeps_done(self) -> int:
+        return ising_info(self._h)[2]
+
+    def close(self):
+        if self._h is not None:
+            h, self._h = self._h, None
+            ising_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

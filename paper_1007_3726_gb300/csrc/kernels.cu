@@ -1,0 +1,359 @@
+// Multi-spin-coded checkerboard Metropolis sweep of the 2D Ising model for
+// sm_103a (after arXiv:1007.3726, Sec. 3-5).
+//
+// Layout: the lattice is L rows of W = L / bits words; bit b of word w of row
+// y is the spin at x = w * bits + b, set = +1 (Sec. 5.2 stores one bit per
+// spin with a set bit meaning +1).
+//
+// Step p updates the sites with (x + y) & 1 == p.  In a row these are the bit
+// positions of one parity, so a word is updated by a masked XOR (Sec. 4: "an
+// additional bit mask ... only allows to flip every second spin").  For each
+// word the thread forms the four neighbour words (Sec. 4: patterns holding the
+// i-th spin's neighbour at bit i): the words above and below, and the row word
+// shifted by one with the carry bit taken from the adjacent word.  The energy
+// variables i_n = s0 ^ s_n (Sec. 4, Eq. 4) are summed bit-parallel with a
+// carry-save adder into "two or more anti-aligned", "exactly one" and "none".
+// The acceptance i1 + i2 + i3 + i4 + 2 exp8 + exp4 >= 2 of Sec. 4, Eq. 5 then
+// reads flip = ge2 | (eq1 & P4) | (eq0 & P8), with P4 / P8 the bit masks of
+// u < thr4 / u < thr8 for the sites' own Philox draws.
+//
+// Each Philox4x32-10 call yields the draws of four consecutive target sites,
+// which in every row occupy one byte of the packed row (x = 8q .. 8q + 7).
+#include "kernels.h"
+
+#include <cstdio>
+
+namespace ising {
+
+namespace {
+
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kWeylA = 0x9E3779B9u;
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+// Ten Philox4x32 rounds in place (SC'11): the two multipliers act on words 0
+// and 2; the new word 0 is hi(B * x2) ^ x1 ^ k0, word 1 is lo(B * x2), word 2
+// is hi(A * x0) ^ x3 ^ k1, word 3 is lo(A * x0).
+__device__ __forceinline__ void philox_rounds(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                              uint32_t &x3, const RoundKeys &k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t pa = (uint64_t)x0 * kPhiloxMulA;
+        const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
+        const uint32_t n0 = (uint32_t)(pb >> 32) ^ x1 ^ k.k0[r];
+        const uint32_t n2 = (uint32_t)(pa >> 32) ^ x3 ^ k.k1[r];
+        x1 = (uint32_t)pb;
+        x3 = (uint32_t)pa;
+        x0 = n0;
+        x2 = n2;
+    }
+}
+
+template <typename Word>
+struct WordTraits;
+template <>
+struct WordTraits<uint32_t> {
+    static constexpr int bits = 32;
+    static constexpr uint32_t even = 0x55555555u;
+    __device__ static int popc(uint32_t v) { return __popc(v); }
+};
+template <>
+struct WordTraits<uint64_t> {
+    static constexpr int bits = 64;
+    static constexpr uint64_t even = 0x5555555555555555ull;
+    __device__ static int popc(uint64_t v) { return __popcll(v); }
+};
+
+// Block-wide sum of two per-thread counters, one 64-bit atomic each per block.
+__device__ __forceinline__ void block_accumulate(unsigned int a, unsigned int b,
+                                                 unsigned long long *acc)
+{
+    __shared__ unsigned long long red[2][32];
+    a = __reduce_add_sync(0xFFFFFFFFu, a);
+    b = __reduce_add_sync(0xFFFFFFFFu, b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = a;
+        red[1][warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        unsigned long long sa = lane < nw ? red[0][lane] : 0ull;
+        unsigned long long sb = lane < nw ? red[1][lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_down_sync(0xFFFFFFFFu, sa, o);
+            sb += __shfl_down_sync(0xFFFFFFFFu, sb, o);
+        }
+        if (lane == 0) {
+            atomicAdd(acc, sa);
+            atomicAdd(acc + 1, sb);
+        }
+    }
+}
+
+// One checkerboard step.  Work item = (block of R rows, word column w); the
+// thread walks down its column keeping the rows above / at / below in
+// registers.  Rows it reads but does not own (the halo rows and the adjacent
+// words) are only used at bit positions of the other parity, which no thread
+// writes during this step.
+template <typename Word>
+__global__ void __launch_bounds__(256) k_half_sweep(const __grid_constant__ HalfSweepArgs a)
+{
+    using Tr = WordTraits<Word>;
+    constexpr int B = Tr::bits;
+    constexpr int NB = B / 8;  // Philox calls (bytes) per word
+    Word *S = static_cast<Word *>(a.spins);
+    const uint64_t L = a.L;
+    const uint32_t W = a.words_per_row;
+    const uint32_t R = a.rows_per_item;
+    const uint64_t nitems = (L / R) * (uint64_t)W;
+    const uint64_t groups_per_row = L >> 3;
+
+    unsigned int cnt_up = 0, cnt_anti = 0;
+    for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems;
+         item += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t rb = item / W;
+        const uint32_t w = (uint32_t)(item - rb * W);
+        const uint32_t wl = (w == 0) ? W - 1 : w - 1;
+        const uint32_t wr = (w + 1 == W) ? 0 : w + 1;
+        const uint64_t y0 = rb * R;
+        Word up = S[((y0 == 0) ? L - 1 : y0 - 1) * W + w];
+        Word cur = S[y0 * W + w];
+        for (uint32_t r = 0; r < R; ++r) {
+            const uint64_t y = y0 + r;
+            const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+            const Word dn = S[yd * W + w];
+            const Word lw = S[y * W + wl];
+            const Word rw = S[y * W + wr];
+            const Word left = (cur << 1) | (lw >> (B - 1));   // bit b holds s(x - 1)
+            const Word right = (cur >> 1) | (rw << (B - 1));  // bit b holds s(x + 1)
+            const uint32_t off = (uint32_t)((y + a.p) & 1u);  // parity of target bit positions
+            const Word mask = off ? (Word)(Tr::even << 1) : Tr::even;
+
+            // energy variables and their bit-sliced sum c = i1 + i2 + i3 + i4
+            const Word i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
+            const Word s12 = i1 ^ i2, c12 = i1 & i2;
+            const Word s34 = i3 ^ i4, c34 = i3 & i4;
+            const Word odd = s12 ^ s34;                  // c odd
+            const Word ge2 = c12 | c34 | (s12 & s34);    // c >= 2: dE <= 0, always accepted
+            const Word eq1 = odd & ~ge2;                 // c == 1: dE = 4
+            const Word eq0 = ~(odd | ge2);               // c == 0: dE = 8
+
+            // the sites' draws: byte q of the word holds four target sites
+            Word p4 = 0, p8 = 0;
+            const uint64_t g0 = y * groups_per_row + (uint64_t)w * NB;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const uint64_t g = g0 + q;
+                uint32_t x0 = (uint32_t)g, x1 = (uint32_t)(g >> 32), x2 = a.t, x3 = a.c3;
+                philox_rounds(x0, x1, x2, x3, a.key);
+                const uint32_t u[4] = {x0, x1, x2, x3};
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const Word bit = (Word)1 << (8 * q + 2 * l);
+                    p4 |= (u[l] < a.thr4) ? bit : (Word)0;
+                    p8 |= (u[l] < a.thr8) ? bit : (Word)0;
+                }
+            }
+            p4 <<= off;
+            p8 <<= off;
+            const Word flip = mask & (ge2 | (eq1 & p4) | (eq0 & p8));
+            const Word nw = cur ^ flip;
+            S[y * W + w] = nw;
+            if (a.acc) {
+                // after the step: +1 spins of the word, and the anti-aligned
+                // bonds of its target sites (their neighbours are final)
+                cnt_up += Tr::popc(nw);
+                cnt_anti += Tr::popc(mask & (nw ^ up)) + Tr::popc(mask & (nw ^ dn)) +
+                            Tr::popc(mask & (nw ^ left)) + Tr::popc(mask & (nw ^ right));
+            }
+            up = nw;
+            cur = dn;
+        }
+    }
+    if (a.acc) block_accumulate(cnt_up, cnt_anti, a.acc);
+}
+
+template <typename Word>
+__global__ void k_init_hot(Word *S, uint64_t nwords, uint64_t L, RoundKeys key, uint32_t c3)
+{
+    constexpr int B = WordTraits<Word>::bits;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t n0 = i * B;  // first site of the word (row-major site index)
+        uint32_t x0 = (uint32_t)(n0 >> 7), x1 = (uint32_t)(n0 >> 39), x2 = 0xFFFFFFFFu, x3 = c3;
+        philox_rounds(x0, x1, x2, x3, key);
+        const uint32_t o[4] = {x0, x1, x2, x3};
+        const uint32_t k = (uint32_t)((n0 >> 5) & 3u);
+        if (B == 32) {
+            S[i] = (Word)o[k];
+        } else {
+            // k is 0 or 2 for a 64-bit word
+            S[i] = (Word)((uint64_t)o[k] | ((uint64_t)o[k + 1] << 32));
+        }
+    }
+}
+
+template <typename Word>
+__global__ void k_pack(const int8_t *src, Word *S, uint64_t nwords, unsigned int *bad)
+{
+    constexpr int B = WordTraits<Word>::bits;
+    unsigned int nbad = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const int8_t *p = src + i * B;
+        Word v = 0;
+#pragma unroll 8
+        for (int b = 0; b < B; ++b) {
+            const int8_t s = p[b];
+            v |= (Word)(s > 0) << b;
+            nbad += (s != 1 && s != -1);
+        }
+        S[i] = v;
+    }
+    if (nbad) atomicAdd(bad, nbad);
+}
+
+template <typename Word>
+__global__ void k_unpack(const Word *S, uint64_t L, uint64_t row0, uint64_t nrows, int8_t *dst)
+{
+    const uint64_t n = nrows * L;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        constexpr int B = WordTraits<Word>::bits;
+        const uint64_t r = i / L, x = i - r * L;
+        const uint64_t y = (row0 + r) % L;
+        const Word w = S[y * (L / B) + x / B];
+        dst[i] = ((w >> (x % B)) & 1) ? 1 : -1;
+    }
+}
+
+template <typename Word>
+__global__ void k_recount(const Word *S, uint64_t L, unsigned long long *acc)
+{
+    using Tr = WordTraits<Word>;
+    constexpr int B = Tr::bits;
+    const uint64_t W = L / B;
+    const uint64_t nwords = L * W;
+    unsigned int up = 0, anti = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t y = i / W, w = i - y * W;
+        const Word s = S[i];
+        const Word dn = S[((y + 1 == L) ? 0 : y + 1) * W + w];
+        const Word nx = S[y * W + ((w + 1 == W) ? 0 : w + 1)];
+        const Word right = (s >> 1) | (nx << (B - 1));
+        up += Tr::popc(s);
+        anti += Tr::popc(s ^ right) + Tr::popc(s ^ dn);
+    }
+    block_accumulate(up, anti, acc);
+}
+
+int g_num_sms = 0;
+
+int num_sms()
+{
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+int grid_for(uint64_t work, int block, int per_sm)
+{
+    const uint64_t need = (work + block - 1) / block;
+    const uint64_t cap = (uint64_t)num_sms() * per_sm;
+    return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+}  // namespace
+
+RoundKeys make_round_keys(uint64_t seed)
+{
+    RoundKeys k;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k.k0[r] = a;
+        k.k1[r] = b;
+        a += kWeylA;
+        b += kWeylB;
+    }
+    return k;
+}
+
+int half_sweep_blocks_per_sm(uint32_t word_bits, int block)
+{
+    int n = 0;
+    if (word_bits == 64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half_sweep<uint64_t>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half_sweep<uint32_t>, block, 0);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_half_sweep(const HalfSweepArgs &a, uint32_t word_bits, LaunchShape shape,
+                              cudaStream_t s)
+{
+    if (word_bits == 64)
+        k_half_sweep<uint64_t><<<shape.grid, shape.block, 0, s>>>(a);
+    else
+        k_half_sweep<uint32_t><<<shape.grid, shape.block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_hot(void *spins, uint64_t L, uint32_t word_bits, uint64_t seed,
+                            uint32_t stream_id, cudaStream_t s)
+{
+    const RoundKeys k = make_round_keys(seed);
+    const uint64_t nwords = L * (L / word_bits);
+    const int block = 256, grid = grid_for(nwords, block, 8);
+    if (word_bits == 64)
+        k_init_hot<uint64_t><<<grid, block, 0, s>>>((uint64_t *)spins, nwords, L, k, stream_id << 1);
+    else
+        k_init_hot<uint32_t><<<grid, block, 0, s>>>((uint32_t *)spins, nwords, L, k, stream_id << 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const int8_t *src, void *spins, uint64_t L, uint32_t word_bits,
+                        unsigned int *bad, cudaStream_t s)
+{
+    const uint64_t nwords = L * (L / word_bits);
+    const int block = 256, grid = grid_for(nwords, block, 8);
+    if (word_bits == 64)
+        k_pack<uint64_t><<<grid, block, 0, s>>>(src, (uint64_t *)spins, nwords, bad);
+    else
+        k_pack<uint32_t><<<grid, block, 0, s>>>(src, (uint32_t *)spins, nwords, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const void *spins, uint64_t L, uint32_t word_bits, uint64_t row0,
+                          uint64_t nrows, int8_t *dst, cudaStream_t s)
+{
+    const int block = 256, grid = grid_for(nrows * L, block, 8);
+    if (word_bits == 64)
+        k_unpack<uint64_t><<<grid, block, 0, s>>>((const uint64_t *)spins, L, row0, nrows, dst);
+    else
+        k_unpack<uint32_t><<<grid, block, 0, s>>>((const uint32_t *)spins, L, row0, nrows, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recount(const void *spins, uint64_t L, uint32_t word_bits,
+                           unsigned long long *acc, cudaStream_t s)
+{
+    const uint64_t nwords = L * (L / word_bits);
+    const int block = 256, grid = grid_for(nwords, block, 8);
+    if (word_bits == 64)
+        k_recount<uint64_t><<<grid, block, 0, s>>>((const uint64_t *)spins, L, acc);
+    else
+        k_recount<uint32_t><<<grid, block, 0, s>>>((const uint32_t *)spins, L, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

@@ -1,0 +1,101 @@
+"""The C-ABI library builds, loads and exports every symbol declared in include/*.h,
+and its host-only logic (thresholds, validation, errors) behaves as declared.
+No compute call is made here, so these run without a GPU."""
+import ctypes
+import glob
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and
+                                not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="needs nvcc to build libising")
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import paper_1007_3726_gb300 as P
+
+    P.build()
+    P.load()
+    return P
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\bISING_API\b[^;{]*?\b(ising_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_core_entry_points():
+    names = _declared_functions()
+    for core in ("ising_create", "ising_sweep", "ising_measure", "ising_destroy"):
+        assert core in names
+    assert len(names) >= 12
+
+
+def test_library_exports_every_declared_symbol(ising):
+    lib = ctypes.CDLL(ising.LIB_PATH)
+    missing = [n for n in sorted(_declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_exports_nothing_else(ising):
+    import subprocess
+
+    out = subprocess.run(["nm", "-D", "--defined-only", ising.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert exported <= _declared_functions(), exported - _declared_functions()
+
+
+def test_library_thresholds_equal_oracle(ising, orc):
+    rng = np.random.default_rng(1)
+    temps = [0.01, 0.5, 1.0, 1.5, 2.0, 2.2, 2.246493, 2.269185, 2.35, 3.5, 1e300]
+    temps += list(rng.uniform(0.2, 20.0, size=500))
+    for T in temps:
+        assert ising.ising_thresholds(float(T)) == orc.thresholds(float(T)), T
+    # the published configurations' values
+    assert ising.ising_thresholds(2.269185) == (736899708, 126431970)
+    assert ising.ising_thresholds(2.0) == (581260615, 78665070)
+
+
+@pytest.mark.parametrize("bad", [0.0, -2.0, float("nan"), float("inf")])
+def test_library_rejects_bad_temperature(ising, bad):
+    with pytest.raises(ising.IsingError) as ei:
+        ising.ising_thresholds(bad)
+    assert ei.value.status == ising.ERR_INVALID
+    assert "finite" in ising.ising_last_error()
+
+
+@pytest.mark.parametrize("field,value", [("L", 0), ("L", 32), ("L", 100), ("L", 2 ** 21),
+                                         ("T", -1.0), ("T", float("nan")),
+                                         ("stream_id", 2 ** 31), ("word_bits", 16),
+                                         ("init", 9), ("init", 3)])
+def test_create_validates_before_touching_the_gpu(ising, field, value):
+    p = ising.IsingParams(L=256, T=2.0, seed=1, stream_id=0, init=2, init_data=None, word_bits=0)
+    setattr(p, field, value)
+    h = ctypes.c_void_p(123)
+    st = ising.load().ising_create(ctypes.byref(p), None, ctypes.byref(h))
+    assert st == ising.ERR_INVALID
+    assert h.value is None
+    assert ising.ising_last_error() != ""
+
+
+def test_null_handles_and_arguments(ising):
+    lib = ising.load()
+    assert lib.ising_destroy(None) == ising.OK
+    assert lib.ising_sweep(None, 1, 0, None, None, 0) == ising.ERR_INVALID
+    assert lib.ising_measure(None, None) == ising.ERR_INVALID
+    assert lib.ising_create(None, None, None) == ising.ERR_INVALID
+    a = ising.ALLOC_FN(lambda n, s, c: None)
+    assert lib.ising_set_allocator(a, ctypes.cast(None, ising.FREE_FN), None) == ising.ERR_INVALID
