@@ -1,0 +1,43 @@
+"""Command-line runner: one lattice through the C ABI, observables as JSON.
+
+    python -m paper_1007_3726_gb300 --L 32768 --T 2.269185 --seed 7 --init hot \
+        --sweeps 1000 --record-every 1 [--word-bits 32] [--time]
+"""
+import argparse
+import json
+import sys
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(prog="python -m paper_1007_3726_gb300")
+    ap.add_argument("--L", type=int, default=1024)
+    ap.add_argument("--T", type=float, default=2.269185)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--stream-id", type=int, default=0)
+    ap.add_argument("--init", default="hot", choices=["hot", "cold_up", "cold_down"])
+    ap.add_argument("--sweeps", type=int, default=100)
+    ap.add_argument("--record-every", type=int, default=1)
+    ap.add_argument("--word-bits", type=int, default=0)
+    ap.add_argument("--time", action="store_true", help="report wall time of the sweeps")
+    a = ap.parse_args(argv)
+
+    import paper_1007_3726_gb300 as P
+
+    P.load()
+    lat = P.Lattice(a.L, a.T, seed=a.seed, stream_id=a.stream_id, init=a.init, word_bits=a.word_bits)
+    t0 = time.perf_counter()
+    lat.sweep(a.sweeps, a.record_every)
+    d = lat.measure()
+    el = time.perf_counter() - t0
+    d["L"], d["T"], d["word_bits"] = a.L, a.T, lat.word_bits
+    if a.time:
+        d["seconds"] = el
+        d["attempts_per_ns"] = a.L * a.L * a.sweeps / el / 1e9
+    lat.close()
+    print(json.dumps(d))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
