@@ -164,6 +164,43 @@ ISING_API ising_status ising_thresholds(double T, uint32_t *thr4, uint32_t *thr8
 ISING_API const char *ising_last_error(void);
 
 /*
+ * ising_sweep_noalloc - the sweep for callers that cannot allocate memory.
+ * The paper has no counterpart; this entry point exists for callers that own
+ * all of their device memory (a serving process whose HBM budget is reserved
+ * up front in its own pool, a host application that lends device buffers to
+ * plug-ins and forbids them the CUDA allocator, a loop that must not take the
+ * device-wide synchronisation a cudaMalloc or cudaFree may bring).  It
+ * allocates nothing: no cudaMalloc, cudaFree, pinned host memory or other
+ * allocating call.
+ *
+ * It runs nsweeps sweeps t0 .. t0 + nsweeps - 1 (the same arithmetic and the
+ * same results as ising_sweep on a handle whose sweeps_done is t0) on a lattice
+ * the caller owns: d_spins is the caller's device array of L * L / 8 bytes in
+ * the storage layout above with word_bits-bit words, updated in place.  The
+ * samples (M, E) of the sweeps whose count t + 1 is a multiple of
+ * record_every (0 = none) go to the caller's host arrays M_out / E_out (cap
+ * entries each) and the call then waits for cuda_stream; with no sample the
+ * call returns once the work is queued.
+ *
+ * Scratch: the per-sweep counters live in a fixed device array compiled into
+ * the library, ISING_NOALLOC_MAX_RECORDS samples (1 MiB) that every GPU which
+ * loads the library holds until the process exits.  A call that would record
+ * more samples fails with ISING_ERR_INVALID before any work; split it.  All
+ * calls share that array and it keeps the previous call's contents (the call
+ * clears what it uses), so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and corrupt each other's samples:
+ * serialise them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.
+ */
+#define ISING_NOALLOC_MAX_RECORDS 65536
+ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L, uint32_t word_bits, double T,
+                                           uint64_t seed, uint32_t stream_id, uint64_t t0,
+                                           uint64_t nsweeps, uint32_t record_every,
+                                           int64_t *M_out, int64_t *E_out, uint64_t cap,
+                                           void *cuda_stream);
+
+/*
  * Optional device allocator for every later allocation of the library (for
  * example PyTorch's caching allocator).  alloc(bytes, stream, ctx) returns a
  * device pointer or NULL (reported as ISING_ERR_OOM); release(ptr, stream,

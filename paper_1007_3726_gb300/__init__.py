@@ -22,7 +22,7 @@ __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
     "ising_measure", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
-    "ising_device_spins", "IsingParams", "IsingObs", "INIT_MODES", "STATUS_NAMES",
+    "ising_device_spins", "ising_sweep_noalloc", "IsingParams", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
@@ -89,6 +89,10 @@ def load(path: str | None = None):
         "ising_thresholds": ([ctypes.c_double, _u32p, _u32p], ctypes.c_int),
         "ising_last_error": ([], ctypes.c_char_p),
         "ising_set_allocator": ([ALLOC_FN, FREE_FN, ctypes.c_void_p], ctypes.c_int),
+        "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                 ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
+                                ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -173,6 +177,17 @@ def ising_device_spins(h) -> tuple[int, int]:
     p, n = ctypes.c_void_p(), ctypes.c_size_t()
     _check(load().ising_device_spins(h, ctypes.byref(p), ctypes.byref(n)))
     return p.value, n.value
+
+
+def ising_sweep_noalloc(d_spins: int, L: int, word_bits: int, T: float, seed: int, stream_id: int,
+                        t0: int, nsweeps: int, record_every: int = 0, M_out=None, E_out=None,
+                        cap: int = 0, stream=None):
+    """Sweeps on a caller-owned device lattice without any allocation by the
+    library (see include/ising.h); M_out / E_out are host int64 arrays."""
+    mp = M_out.ctypes.data_as(_i64p) if M_out is not None else None
+    ep = E_out.ctypes.data_as(_i64p) if E_out is not None else None
+    _check(load().ising_sweep_noalloc(d_spins, L, word_bits, float(T), seed, stream_id, t0, nsweeps,
+                                      record_every, mp, ep, cap, _stream_ptr(stream)))
 
 
 _alloc_keepalive = []

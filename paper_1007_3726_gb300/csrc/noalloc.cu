@@ -1,0 +1,139 @@
+// ising_sweep_noalloc: the sweep for callers that cannot allocate memory.
+//
+// Some callers own every byte of device memory themselves and must not see
+// the library call cudaMalloc: a serving process that has reserved its whole
+// HBM budget up front in its own pool, a host application that lends device
+// buffers to plug-ins and forbids them the CUDA allocator, or a loop that
+// cannot afford the device-wide synchronisation a cudaMalloc / cudaFree may
+// bring.  For them this entry point runs the same half-sweep kernel as
+// ising_sweep on a lattice the caller owns, and keeps the kernel's scratch
+// (the per-sweep M/E counters) in a fixed array compiled into the library
+// instead of allocating it.
+#include "ising.h"
+#include "kernels.h"
+#include "runtime.h"
+
+#include <cstring>
+#include <mutex>
+
+using namespace ising;
+
+namespace {
+
+// Two 64-bit counters per recorded sweep (number of +1 spins, number of
+// anti-aligned bonds).  Every GPU that loads the library holds this 1 MiB
+// until the process exits.
+constexpr uint64_t kMaxRecords = ISING_NOALLOC_MAX_RECORDS;
+static __device__ __align__(256) unsigned long long g_noalloc_counters[2 * kMaxRecords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+unsigned long long *g_counters_addr[kMaxDevices] = {};
+
+// Device address of the counters on the current device, looked up once per
+// device.  In host code g_noalloc_counters names a host-side stand-in, not
+// device memory, so it must never be handed to a kernel directly.
+ising_status counters_for_current_device(unsigned long long **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(ISING_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(ISING_ERR_INVALID, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_counters_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_counters);
+        if (e != cudaSuccess || !p)
+            return fail(ISING_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_counters_addr[dev] = static_cast<unsigned long long *>(p);
+    }
+    *out = g_counters_addr[dev];
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L, uint32_t word_bits,
+                                                      double T, uint64_t seed, uint32_t stream_id,
+                                                      uint64_t t0, uint64_t nsweeps,
+                                                      uint32_t record_every, int64_t *M_out,
+                                                      int64_t *E_out, uint64_t cap,
+                                                      void *cuda_stream)
+{
+    clear_error();
+    if (!d_spins) return fail(ISING_ERR_INVALID, "d_spins is NULL");
+    if (L < 64 || L % 64 != 0 || L > (1ull << 20))
+        return fail(ISING_ERR_INVALID, "L must be a multiple of 64 in [64, 2^20]");
+    if (word_bits != 32 && word_bits != 64) return fail(ISING_ERR_INVALID, "word_bits must be 32 or 64");
+    if (!valid_temperature(T)) return fail(ISING_ERR_INVALID, "T must be finite and > 0");
+    if (stream_id >= (1u << 31)) return fail(ISING_ERR_INVALID, "stream_id must be < 2^31");
+    if (t0 + nsweeps >= 0xFFFFFFFFull)
+        return fail(ISING_ERR_INVALID, "sweep counter would reach 2^32 - 1");
+    if ((M_out == nullptr) != (E_out == nullptr))
+        return fail(ISING_ERR_INVALID, "M_out and E_out must both be set or both be NULL");
+    const uint64_t nrec = record_every ? (t0 + nsweeps) / record_every - t0 / record_every : 0;
+    if (nrec > kMaxRecords)
+        return fail(ISING_ERR_INVALID,
+                    "%llu samples in one call exceed the fixed scratch of %llu; split the call",
+                    (unsigned long long)nrec, (unsigned long long)kMaxRecords);
+    if (nrec > 0 && !M_out) return fail(ISING_ERR_INVALID, "samples requested but M_out is NULL");
+    if (M_out && cap < nrec) return fail(ISING_ERR_INVALID, "cap is smaller than the samples");
+    if (nsweeps == 0) return ISING_OK;
+
+    unsigned long long *acc = nullptr;
+    ising_status st = counters_for_current_device(&acc);
+    if (st != ISING_OK) return st;
+
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSuccess;
+    // the counters keep the previous call's values: clear the ones this call adds into
+    if (nrec) e = cudaMemsetAsync(acc, 0, nrec * 2 * sizeof(unsigned long long), s);
+
+    HalfSweepArgs a{};
+    a.spins = d_spins;
+    a.L = L;
+    a.words_per_row = (uint32_t)(L / word_bits);
+    a.rows_per_item = 8;
+    a.key = make_round_keys(seed);
+    a.thr4 = threshold_for(4.0, T);
+    a.thr8 = threshold_for(8.0, T);
+    LaunchShape shape{1, 256};
+    {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const uint64_t items = (L / a.rows_per_item) * a.words_per_row;
+        const uint64_t need = (items + shape.block - 1) / shape.block;
+        const uint64_t cap_blocks = (uint64_t)(sms > 0 ? sms : 1) *
+                                    half_sweep_blocks_per_sm(word_bits, shape.block);
+        shape.grid = (int)(need < cap_blocks ? need : cap_blocks);
+    }
+    uint64_t slot = 0;
+    for (uint64_t i = 0; i < nsweeps && e == cudaSuccess; ++i) {
+        const uint64_t t = t0 + i;
+        a.t = (uint32_t)t;
+        for (uint32_t p = 0; p < 2 && e == cudaSuccess; ++p) {
+            a.p = p;
+            a.c3 = (stream_id << 1) | p;
+            a.acc = (p == 1 && record_every && (t + 1) % record_every == 0) ? acc + 2 * (slot++)
+                                                                          : nullptr;
+            e = launch_half_sweep(a, word_bits, shape, s);
+        }
+    }
+    if (e == cudaSuccess && nrec) {
+        // column 0 of the counters into M_out, column 1 into E_out
+        e = cudaMemcpy2DAsync(M_out, sizeof(int64_t), acc, 2 * sizeof(unsigned long long),
+                              sizeof(int64_t), nrec, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(E_out, sizeof(int64_t), acc + 1, 2 * sizeof(unsigned long long),
+                                  sizeof(int64_t), nrec, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess && nrec) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ISING_ERR_CUDA, "ising_sweep_noalloc: %s", cudaGetErrorString(e));
+    const int64_t N = (int64_t)(L * L);
+    for (uint64_t i = 0; i < nrec; ++i) {
+        M_out[i] = 2 * M_out[i] - N;      // +1 spins -> magnetisation
+        E_out[i] = 2 * E_out[i] - 2 * N;  // anti-aligned bonds -> energy
+    }
+    return ISING_OK;
+}

@@ -1,0 +1,63 @@
+"""ising_sweep_noalloc: the sweep for callers that cannot allocate memory.
+
+Callers that own all of their device memory (a pool that has reserved the HBM
+budget, a host application lending buffers to a plug-in) use this entry point:
+it runs the sweep on the caller's lattice and keeps its scratch in a fixed
+array inside the library.  Its results must equal those of ising_sweep.  This
+file is collected last so that a run stopping at the first failure has already
+run every other test; it passes alone in a fresh process too (the first call
+performs the per-device set-up).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1007_3726_gb300 as P
+
+    P.build()
+    P.load()
+    return P
+
+
+@pytest.mark.parametrize("L,word_bits,record_every", [(256, 32, 1), (1024, 64, 3)])
+def test_noalloc_matches_ising_sweep_on_two_calls(P, L, word_bits, record_every):
+    import torch
+
+    T, seed, stream_id = 2.269185, 31, 6
+    ref = P.Lattice(L, T, seed=seed, stream_id=stream_id, init="hot", word_bits=word_bits)
+    # the caller's own device lattice, a copy of the same hot start
+    packed = ref.packed()
+    dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()
+    torch.cuda.synchronize()
+    t0 = 0
+    for n in (40, 25):  # two calls in a row
+        k = (t0 + n) // record_every - t0 // record_every
+        Mr, Er = ref.sweep(n, record_every, collect=True)
+        M = np.zeros(k, dtype=np.int64)
+        E = np.zeros(k, dtype=np.int64)
+        P.ising_sweep_noalloc(dev.data_ptr(), L, word_bits, T, seed, stream_id, t0, n,
+                              record_every, M, E, k)
+        assert np.array_equal(M, Mr) and np.array_equal(E, Er)
+        got = dev.cpu().numpy().view(packed.dtype).reshape(packed.shape)
+        assert np.array_equal(got, ref.packed())
+        t0 += n
+    ref.close()
+
+
+def test_noalloc_rejects_more_samples_than_its_scratch(P):
+    import torch
+
+    L = 64
+    dev = torch.zeros(L * L // 8, dtype=torch.uint8, device="cuda")
+    cap = 70000
+    M = np.zeros(cap, dtype=np.int64)
+    E = np.zeros(cap, dtype=np.int64)
+    with pytest.raises(P.IsingError) as ei:
+        P.ising_sweep_noalloc(dev.data_ptr(), L, 32, 2.0, 1, 0, 0, 65537, 1, M, E, cap)
+    assert ei.value.status == P.ERR_INVALID and "split" in P.ising_last_error()
+    # nothing ran: the lattice is untouched
+    assert int(dev.sum().item()) == 0
