@@ -142,7 +142,7 @@ def profiled_traffic():
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"kernels\.cu sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
+    m = re.search(r"kernels\.cu`?\s+sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
     t = re.search(r"dram bytes per launch:\s*`?([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != kernel_source_hash():
         return None
