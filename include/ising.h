@@ -163,6 +163,40 @@ ISING_API ising_status ising_thresholds(double T, uint32_t *thr4, uint32_t *thr8
 /* Thread-local text of the last failure on this thread ("" if none). */
 ISING_API const char *ising_last_error(void);
 
+/* ---- launch configuration and autotuning ------------------------------- */
+
+/*
+ * A launch configuration of the half-sweep kernel (Sec. 5.2 leaves block and
+ * thread counts to the implementation).  Every valid configuration gives
+ * bit-identical lattices and samples; they differ only in speed.
+ *   proc_bits      32 or 64: lattice bits one thread updates per row (any
+ *                  storage word width can be processed either way)
+ *   regcap         0: compiler's register choice, 1: <= 40, 2: <= 32 per thread
+ *   block          threads per block: 128, 256 or 512
+ *   rows_per_item  rows one thread walks down per work item (divides L, <= 64)
+ *   grid           blocks, 0 = as many as can be resident at once
+ */
+typedef struct {
+    uint32_t proc_bits, regcap, block, rows_per_item, grid;
+} ising_launch;
+
+/* The handle's current configuration. */
+ISING_API ising_status ising_get_launch(const ising_lattice *h, ising_launch *out);
+/* Replaces it (ISING_ERR_INVALID if not valid for the handle's L). */
+ISING_API ising_status ising_set_launch(ising_lattice *h, const ising_launch *cfg);
+/* Writes up to cap candidate configurations for lattices of size L to out and
+ * returns how many there are in total (out may be NULL to count). */
+ISING_API uint32_t ising_launch_candidates(uint64_t L, ising_launch *out, uint32_t cap);
+/*
+ * Times every candidate (reps timed step pairs each, after one untimed pair)
+ * on a scratch copy of up to 256 MiB of the handle's rows, installs the
+ * fastest on the handle, remembers it for later handles of the same L and
+ * word width on this device, and returns it with its mean time per step in
+ * microseconds.  The lattice itself is not changed.  Waits for the GPU.
+ */
+ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_launch *best,
+                                      double *best_us_per_step);
+
 /*
  * ising_sweep_noalloc - the sweep for callers that cannot allocate memory.
  * The paper has no counterpart; this entry point exists for callers that own

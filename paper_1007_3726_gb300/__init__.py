@@ -22,7 +22,8 @@ __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
     "ising_measure", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
-    "ising_device_spins", "ising_sweep_noalloc", "IsingParams", "IsingObs", "INIT_MODES", "STATUS_NAMES",
+    "ising_device_spins", "ising_sweep_noalloc", "ising_get_launch", "ising_set_launch",
+    "ising_launch_candidates", "ising_autotune", "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
@@ -50,6 +51,14 @@ class IsingObs(ctypes.Structure):
                 ("mean_m2", ctypes.c_double), ("mean_m4", ctypes.c_double),
                 ("mean_e", ctypes.c_double), ("mean_e2", ctypes.c_double),
                 ("U4", ctypes.c_double), ("chi", ctypes.c_double), ("C", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IsingLaunch(ctypes.Structure):
+    _fields_ = [("proc_bits", ctypes.c_uint32), ("regcap", ctypes.c_uint32), ("block", ctypes.c_uint32),
+                ("rows_per_item", ctypes.c_uint32), ("grid", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +98,12 @@ def load(path: str | None = None):
         "ising_thresholds": ([ctypes.c_double, _u32p, _u32p], ctypes.c_int),
         "ising_last_error": ([], ctypes.c_char_p),
         "ising_set_allocator": ([ALLOC_FN, FREE_FN, ctypes.c_void_p], ctypes.c_int),
+        "ising_get_launch": ([H, ctypes.POINTER(IsingLaunch)], ctypes.c_int),
+        "ising_set_launch": ([H, ctypes.POINTER(IsingLaunch)], ctypes.c_int),
+        "ising_launch_candidates": ([ctypes.c_uint64, ctypes.POINTER(IsingLaunch), ctypes.c_uint32],
+                                    ctypes.c_uint32),
+        "ising_autotune": ([H, ctypes.c_uint32, ctypes.POINTER(IsingLaunch),
+                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
@@ -190,6 +205,30 @@ def ising_sweep_noalloc(d_spins: int, L: int, word_bits: int, T: float, seed: in
                                       record_every, mp, ep, cap, _stream_ptr(stream)))
 
 
+def ising_get_launch(h) -> dict:
+    o = IsingLaunch()
+    _check(load().ising_get_launch(h, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def ising_set_launch(h, cfg: dict):
+    _check(load().ising_set_launch(h, ctypes.byref(IsingLaunch(**cfg))))
+
+
+def ising_launch_candidates(L: int) -> list[dict]:
+    n = load().ising_launch_candidates(L, None, 0)
+    arr = (IsingLaunch * max(n, 1))()
+    load().ising_launch_candidates(L, arr, n)
+    return [arr[i].as_dict() for i in range(n)]
+
+
+def ising_autotune(h, reps: int = 3) -> tuple[dict, float]:
+    o = IsingLaunch()
+    us = ctypes.c_double()
+    _check(load().ising_autotune(h, reps, ctypes.byref(o), ctypes.byref(us)))
+    return o.as_dict(), us.value
+
+
 _alloc_keepalive = []
 
 
@@ -280,6 +319,19 @@ class Lattice:
 
     def recount(self) -> tuple[int, int]:
         return ising_recount(self._h)
+
+    @property
+    def launch(self) -> dict:
+        return ising_get_launch(self._h)
+
+    def set_launch(self, **cfg):
+        full = dict(self.launch)
+        full.update(cfg)
+        ising_set_launch(self._h, full)
+
+    def autotune(self, reps: int = 3) -> tuple[dict, float]:
+        """Pick the fastest launch configuration (results do not depend on it)."""
+        return ising_autotune(self._h, reps)
 
     @property
     def sweeps_done(self) -> int:

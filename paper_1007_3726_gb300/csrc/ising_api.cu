@@ -3,6 +3,7 @@
 // FP64 moments.  All lattice arithmetic runs in the kernels of kernels.cu.
 #include "ising.h"
 #include "kernels.h"
+#include "handle.h"
 #include "runtime.h"
 
 #include <cmath>
@@ -86,37 +87,7 @@ bool valid_temperature(double T) { return std::isfinite(T) && T > 0.0; }
 
 }  // namespace ising
 
-// ------------------------------------------------------------ handle -------
-struct ising_lattice {
-    uint64_t L = 0;
-    double T = 0;
-    uint64_t seed = 0;
-    uint32_t stream_id = 0;
-    uint32_t word_bits = 32;
-    uint32_t W = 0;  // words per row
-    uint32_t thr4 = 0, thr8 = 0;
-    size_t bytes = 0;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    Allocator alloc;
-    void *d_spins = nullptr;
-    unsigned long long *d_acc = nullptr;  // 2 counters per slot
-    unsigned long long *h_acc = nullptr;  // pinned mirror
-    size_t acc_slots = 0;
-    cudaEvent_t ev = nullptr;
-    RoundKeys key{};
-    LaunchShape shape{1, 256};
-    uint32_t rows_per_item = 8;
-    uint64_t sweeps_done = 0;
-    int64_t M = 0, E = 0;
-    std::vector<int64_t> sM, sE;
-    // samples of the last queued call, read back at the next synchronising call
-    bool pending = false;
-    size_t pending_rec = 0;  // recorded slots of that call
-    bool failed = false;
-};
-
-namespace {
+namespace ising {
 
 int64_t to_M(const ising_lattice *h, unsigned long long up)
 {
@@ -210,10 +181,6 @@ ising_status count_state(ising_lattice *h)
     return ISING_OK;
 }
 
-}  // namespace
-
-namespace ising {
-
 ising_status validate_params(const ising_params *p, uint32_t *word_bits)
 {
     if (!p) return fail(ISING_ERR_INVALID, "params is NULL");
@@ -304,18 +271,7 @@ ising_status ising_create(const ising_params *params, void *cuda_stream, ising_l
         return bail(fail(ISING_ERR_OOM, "cannot allocate %zu bytes for the lattice", h->bytes));
     if ((st = ensure_acc(h, 64)) != ISING_OK) return bail(st);
 
-    // default launch shape: a persistent-style grid of resident blocks
-    h->rows_per_item = 8;
-    h->shape.block = 256;
-    {
-        const uint64_t items = (h->L / h->rows_per_item) * h->W;
-        const int per_sm = half_sweep_blocks_per_sm(wb, h->shape.block);
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-        const uint64_t need = (items + h->shape.block - 1) / h->shape.block;
-        const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * per_sm;
-        h->shape.grid = (int)(need < cap ? need : cap);
-    }
+    h->launch = default_launch(h->device, h->L, wb);
 
     // initial state
     switch (params->init) {
@@ -395,8 +351,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
     HalfSweepArgs a{};
     a.spins = h->d_spins;
     a.L = h->L;
-    a.words_per_row = h->W;
-    a.rows_per_item = h->rows_per_item;
+    a.rows = h->L;
     a.key = h->key;
     a.thr4 = h->thr4;
     a.thr8 = h->thr8;
@@ -415,7 +370,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
                 else if (i + 1 == nsweeps)
                     a.acc = h->d_acc + 2 * nrec;  // state after the call
             }
-            CK(h, launch_half_sweep(a, h->word_bits, h->shape, h->stream));
+            CK(h, launch_half_sweep(a, h->launch, h->stream));
         }
     }
     if (slot == nrec && nrec > 0 && record_every && (t0 + nsweeps) % record_every == 0) {

@@ -32,14 +32,15 @@ constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
 constexpr uint32_t kWeylA = 0x9E3779B9u;
 constexpr uint32_t kWeylB = 0xBB67AE85u;
 
-// Ten Philox4x32 rounds in place (SC'11): the two multipliers act on words 0
-// and 2; the new word 0 is hi(B * x2) ^ x1 ^ k0, word 1 is lo(B * x2), word 2
-// is hi(A * x0) ^ x3 ^ k1, word 3 is lo(A * x0).
-__device__ __forceinline__ void philox_rounds(uint32_t &x0, uint32_t &x1, uint32_t &x2,
-                                              uint32_t &x3, const RoundKeys &k)
+// Philox4x32 rounds r0 .. 9 in place (SC'11): the two multipliers act on
+// words 0 and 2; the new word 0 is hi(B * x2) ^ x1 ^ k0, word 1 is lo(B * x2),
+// word 2 is hi(A * x0) ^ x3 ^ k1, word 3 is lo(A * x0).
+template <int R0>
+__device__ __forceinline__ void philox_rounds_from(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                                   uint32_t &x3, const RoundKeys &k)
 {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = R0; r < 10; ++r) {
         const uint64_t pa = (uint64_t)x0 * kPhiloxMulA;
         const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
         const uint32_t n0 = (uint32_t)(pb >> 32) ^ x1 ^ k.k0[r];
@@ -51,6 +52,12 @@ __device__ __forceinline__ void philox_rounds(uint32_t &x0, uint32_t &x1, uint32
     }
 }
 
+__device__ __forceinline__ void philox_rounds(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                              uint32_t &x3, const RoundKeys &k)
+{
+    philox_rounds_from<0>(x0, x1, x2, x3, k);
+}
+
 template <typename Word>
 struct WordTraits;
 template <>
@@ -58,12 +65,17 @@ struct WordTraits<uint32_t> {
     static constexpr int bits = 32;
     static constexpr uint32_t even = 0x55555555u;
     __device__ static int popc(uint32_t v) { return __popc(v); }
+    __device__ static uint32_t from_halves(const uint32_t *h) { return h[0]; }
 };
 template <>
 struct WordTraits<uint64_t> {
     static constexpr int bits = 64;
     static constexpr uint64_t even = 0x5555555555555555ull;
     __device__ static int popc(uint64_t v) { return __popcll(v); }
+    __device__ static uint64_t from_halves(const uint32_t *h)
+    {
+        return (uint64_t)h[0] | ((uint64_t)h[1] << 32);
+    }
 };
 
 // Block-wide sum of two per-thread counters, one 64-bit atomic each per block.
@@ -95,37 +107,86 @@ __device__ __forceinline__ void block_accumulate(unsigned int a, unsigned int b,
     }
 }
 
+// The acceptance masks of one word: bit 8q + 2l of half (q / 4) is set when
+// draw l of the word's Philox call q is below the threshold.  Round 1 and the
+// word-0/word-3 half of round 2 are taken from the step-uniform values.
+template <int NB>
+__device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t g0,
+                                                uint32_t (&p4)[(NB + 3) / 4],
+                                                uint32_t (&p8)[(NB + 3) / 4])
+{
+    const uint32_t c1 = (uint32_t)(g0 >> 32);  // the same for all groups of a word
+    uint32_t r2x2k = a.r2x2k, r2x3 = a.r2x3;
+    if (c1 != 0u) {
+        const uint64_t pa = (uint64_t)(a.r1x0 ^ c1) * kPhiloxMulA;
+        r2x2k = (uint32_t)(pa >> 32) ^ a.key.k1[1];
+        r2x3 = (uint32_t)pa;
+    }
+    const uint32_t glo = (uint32_t)g0;
+#pragma unroll
+    for (int h = 0; h < (NB + 3) / 4; ++h) {
+        p4[h] = 0u;
+        p8[h] = 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        // round 1: words 0, 1 are uniform (r1x0 ^ c1, lo(B t))
+        const uint64_t pa = (uint64_t)(glo + (uint32_t)q) * kPhiloxMulA;
+        const uint32_t x2 = (uint32_t)(pa >> 32) ^ a.r1x2k;
+        const uint32_t x3 = (uint32_t)pa;
+        // round 2: the product A * word 0 is uniform per word
+        const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
+        uint32_t y0 = (uint32_t)(pb >> 32) ^ a.r2x0k;
+        uint32_t y1 = (uint32_t)pb;
+        uint32_t y2 = x3 ^ r2x2k;
+        uint32_t y3 = r2x3;
+        philox_rounds_from<2>(y0, y1, y2, y3, a.key);
+        const uint32_t u[4] = {y0, y1, y2, y3};
+        const int h = q >> 2;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const uint32_t bit = 1u << (8 * (q & 3) + 2 * l);
+            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+                : "+r"(p4[h])
+                : "r"(u[l]), "r"(a.thr4), "r"(bit));
+            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+                : "+r"(p8[h])
+                : "r"(u[l]), "r"(a.thr8), "r"(bit));
+        }
+    }
+}
+
 // One checkerboard step.  Work item = (block of R rows, word column w); the
 // thread walks down its column keeping the rows above / at / below in
 // registers.  Rows it reads but does not own (the halo rows and the adjacent
 // words) are only used at bit positions of the other parity, which no thread
 // writes during this step.
 template <typename Word>
-__global__ void __launch_bounds__(256) k_half_sweep(const __grid_constant__ HalfSweepArgs a)
+__device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
 {
     using Tr = WordTraits<Word>;
     constexpr int B = Tr::bits;
     constexpr int NB = B / 8;  // Philox calls (bytes) per word
     Word *S = static_cast<Word *>(a.spins);
-    const uint64_t L = a.L;
+    const uint64_t rows = a.rows;
     const uint32_t W = a.words_per_row;
     const uint32_t R = a.rows_per_item;
-    const uint64_t nitems = (L / R) * (uint64_t)W;
-    const uint64_t groups_per_row = L >> 3;
+    const uint32_t nrb = (uint32_t)(rows / R);
+    const uint64_t groups_per_row = a.L >> 3;
 
     unsigned int cnt_up = 0, cnt_anti = 0;
-    for (uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; item < nitems;
-         item += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t rb = item / W;
-        const uint32_t w = (uint32_t)(item - rb * W);
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t rb = tid / W;
+    uint32_t w = tid - rb * W;
+    while (rb < nrb) {
         const uint32_t wl = (w == 0) ? W - 1 : w - 1;
         const uint32_t wr = (w + 1 == W) ? 0 : w + 1;
-        const uint64_t y0 = rb * R;
-        Word up = S[((y0 == 0) ? L - 1 : y0 - 1) * W + w];
+        const uint64_t y0 = (uint64_t)rb * R;
+        Word up = S[((y0 == 0) ? rows - 1 : y0 - 1) * W + w];
         Word cur = S[y0 * W + w];
         for (uint32_t r = 0; r < R; ++r) {
             const uint64_t y = y0 + r;
-            const uint64_t yd = (y + 1 == L) ? 0 : y + 1;
+            const uint64_t yd = (y + 1 == rows) ? 0 : y + 1;
             const Word dn = S[yd * W + w];
             const Word lw = S[y * W + wl];
             const Word rw = S[y * W + wr];
@@ -144,23 +205,10 @@ __global__ void __launch_bounds__(256) k_half_sweep(const __grid_constant__ Half
             const Word eq0 = ~(odd | ge2);               // c == 0: dE = 8
 
             // the sites' draws: byte q of the word holds four target sites
-            Word p4 = 0, p8 = 0;
-            const uint64_t g0 = y * groups_per_row + (uint64_t)w * NB;
-#pragma unroll
-            for (int q = 0; q < NB; ++q) {
-                const uint64_t g = g0 + q;
-                uint32_t x0 = (uint32_t)g, x1 = (uint32_t)(g >> 32), x2 = a.t, x3 = a.c3;
-                philox_rounds(x0, x1, x2, x3, a.key);
-                const uint32_t u[4] = {x0, x1, x2, x3};
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    const Word bit = (Word)1 << (8 * q + 2 * l);
-                    p4 |= (u[l] < a.thr4) ? bit : (Word)0;
-                    p8 |= (u[l] < a.thr8) ? bit : (Word)0;
-                }
-            }
-            p4 <<= off;
-            p8 <<= off;
+            uint32_t h4[(NB + 3) / 4], h8[(NB + 3) / 4];
+            word_draw_masks<NB>(a, y * groups_per_row + (uint64_t)w * NB, h4, h8);
+            const Word p4 = Tr::from_halves(h4) << off;
+            const Word p8 = Tr::from_halves(h8) << off;
             const Word flip = mask & (ge2 | (eq1 & p4) | (eq0 & p8));
             const Word nw = cur ^ flip;
             S[y * W + w] = nw;
@@ -174,8 +222,30 @@ __global__ void __launch_bounds__(256) k_half_sweep(const __grid_constant__ Half
             up = nw;
             cur = dn;
         }
+        rb += a.stride_rb;
+        w += a.stride_w;
+        if (w >= W) {
+            w -= W;
+            ++rb;
+        }
     }
     if (a.acc) block_accumulate(cnt_up, cnt_anti, a.acc);
+}
+
+template <typename Word>
+__global__ void __launch_bounds__(512) k_half_sweep(const __grid_constant__ HalfSweepArgs a)
+{
+    half_sweep_body<Word>(a);
+}
+template <typename Word>
+__global__ void __launch_bounds__(512, 3) k_half_sweep_r40(const __grid_constant__ HalfSweepArgs a)
+{
+    half_sweep_body<Word>(a);
+}
+template <typename Word>
+__global__ void __launch_bounds__(512, 4) k_half_sweep_r32(const __grid_constant__ HalfSweepArgs a)
+{
+    half_sweep_body<Word>(a);
 }
 
 template <typename Word>
@@ -288,23 +358,77 @@ RoundKeys make_round_keys(uint64_t seed)
     return k;
 }
 
-int half_sweep_blocks_per_sm(uint32_t word_bits, int block)
+namespace {
+using HalfSweepKernel = void (*)(HalfSweepArgs);
+
+HalfSweepKernel half_sweep_kernel(const LaunchConfig &c)
+{
+    if (c.proc_bits == 64) {
+        if (c.regcap == 1) return k_half_sweep_r40<uint64_t>;
+        if (c.regcap == 2) return k_half_sweep_r32<uint64_t>;
+        return k_half_sweep<uint64_t>;
+    }
+    if (c.regcap == 1) return k_half_sweep_r40<uint32_t>;
+    if (c.regcap == 2) return k_half_sweep_r32<uint32_t>;
+    return k_half_sweep<uint32_t>;
+}
+
+uint64_t mulA(uint32_t x) { return (uint64_t)x * kPhiloxMulA; }
+uint64_t mulB(uint32_t x) { return (uint64_t)x * kPhiloxMulB; }
+}  // namespace
+
+void prepare_half_sweep(HalfSweepArgs &a, int grid, int block)
+{
+    const uint64_t pb = mulB(a.t);
+    a.r1x0 = (uint32_t)(pb >> 32) ^ a.key.k0[0];
+    a.r1x2k = a.c3 ^ a.key.k1[0];
+    a.r2x0k = (uint32_t)pb ^ a.key.k0[1];
+    const uint64_t pa = mulA(a.r1x0);
+    a.r2x2k = (uint32_t)(pa >> 32) ^ a.key.k1[1];
+    a.r2x3 = (uint32_t)pa;
+    const uint64_t stride = (uint64_t)grid * (uint64_t)block;
+    a.stride_rb = (uint32_t)(stride / a.words_per_row);
+    a.stride_w = (uint32_t)(stride % a.words_per_row);
+}
+
+bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
+{
+    if (c.proc_bits != 32 && c.proc_bits != 64) return false;
+    if (c.regcap > 2) return false;
+    if (c.block != 128 && c.block != 256 && c.block != 512) return false;
+    if (c.rows_per_item < 1 || c.rows_per_item > 64 || rows % c.rows_per_item != 0) return false;
+    if (L % c.proc_bits != 0) return false;
+    // the item index (row block * words + word) and the thread index stay in 32 bits
+    const uint64_t items = rows / c.rows_per_item * (L / c.proc_bits);
+    if (items >= (1ull << 32) - (1ull << 26)) return false;
+    if (c.grid > 65535u * 16u) return false;
+    return true;
+}
+
+int half_sweep_blocks_per_sm(const LaunchConfig &c)
 {
     int n = 0;
-    if (word_bits == 64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half_sweep<uint64_t>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half_sweep<uint32_t>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel(c), (int)c.block, 0);
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_half_sweep(const HalfSweepArgs &a, uint32_t word_bits, LaunchShape shape,
-                              cudaStream_t s)
+int resolve_grid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
-    if (word_bits == 64)
-        k_half_sweep<uint64_t><<<shape.grid, shape.block, 0, s>>>(a);
-    else
-        k_half_sweep<uint32_t><<<shape.grid, shape.block, 0, s>>>(a);
+    const uint64_t items = rows / c.rows_per_item * (L / c.proc_bits);
+    const uint64_t need = (items + c.block - 1) / c.block;
+    uint64_t cap = c.grid;
+    if (cap == 0) cap = (uint64_t)num_sms() * half_sweep_blocks_per_sm(c);
+    const uint64_t g = need < cap ? need : cap;
+    return (int)(g > 0 ? g : 1);
+}
+
+cudaError_t launch_half_sweep(HalfSweepArgs a, const LaunchConfig &c, cudaStream_t s)
+{
+    const int grid = resolve_grid(c, a.L, a.rows);
+    a.words_per_row = (uint32_t)(a.L / c.proc_bits);
+    a.rows_per_item = c.rows_per_item;
+    prepare_half_sweep(a, grid, (int)c.block);
+    half_sweep_kernel(c)<<<grid, c.block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -19,15 +19,25 @@ RoundKeys make_round_keys(uint64_t seed);
 
 // One checkerboard step (Sec. 3) over a packed periodic lattice.
 struct HalfSweepArgs {
-    void *spins;              // L rows of words_per_row words (32- or 64-bit)
-    uint64_t L;
-    uint32_t words_per_row;   // L / word_bits
-    uint32_t rows_per_item;   // rows one thread walks down (divides L)
+    void *spins;              // rows x words_per_row processing words (32- or 64-bit)
+    uint64_t L;               // row length in sites (the lattice is L x L)
+    uint64_t rows;            // rows in the buffer (== L; fewer only for timing runs)
+    uint32_t words_per_row;   // L / processing bits
+    uint32_t rows_per_item;   // rows one thread walks down (divides rows)
     RoundKeys key;
     uint32_t thr4, thr8;      // floor(2^32 exp(-4/T)), floor(2^32 exp(-8/T))
     uint32_t t;               // sweep index (Philox counter word 2)
     uint32_t c3;              // stream_id << 1 | p (Philox counter word 3)
     uint32_t p;               // parity of the updated sites
+    // The parts of Philox rounds 1 and 2 that depend only on (t, c3, key), the
+    // same for every site of the step; filled by prepare_half_sweep().
+    uint32_t r1x0;   // hi(B t) ^ k0[0]: round-1 word 0 before the XOR with counter word 1
+    uint32_t r1x2k;  // c3 ^ k1[0]
+    uint32_t r2x0k;  // lo(B t) ^ k0[1]
+    uint32_t r2x2k;  // hi(A r1x0) ^ k1[1]   (counter word 1 == 0)
+    uint32_t r2x3;   // lo(A r1x0)           (counter word 1 == 0)
+    // grid-stride walk over items (item = row block * words_per_row + word)
+    uint32_t stride_rb, stride_w;  // (grid * block) / words_per_row, (grid * block) % words_per_row
     // If not null (step B only): acc[0] += number of +1 spins of the whole
     // lattice after the step, acc[1] += number of anti-aligned bonds after the
     // step.  Every bond has exactly one endpoint of parity 1, so step B sees
@@ -35,14 +45,25 @@ struct HalfSweepArgs {
     unsigned long long *acc;
 };
 
-struct LaunchShape {
-    int grid;
-    int block;
+// Fills the step-uniform Philox values and the grid-stride constants.
+void prepare_half_sweep(HalfSweepArgs &a, int grid, int block);
+
+// A launch configuration of the half-sweep.  Every valid configuration gives
+// bit-identical results; they differ only in speed.
+struct LaunchConfig {
+    uint32_t proc_bits;      // 32 or 64: bits one thread updates per row
+    uint32_t regcap;         // 0: compiler's choice, 1: <= 40 registers, 2: <= 32 registers
+    uint32_t block;          // 128, 256 or 512 threads
+    uint32_t rows_per_item;  // 2 .. 64, divides L
+    uint32_t grid;           // blocks (0 = all resident blocks of the device)
 };
 
-cudaError_t launch_half_sweep(const HalfSweepArgs &a, uint32_t word_bits, LaunchShape shape,
-                              cudaStream_t s);
-int half_sweep_blocks_per_sm(uint32_t word_bits, int block);
+bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows);
+// Resident blocks per SM of the configuration's kernel.
+int half_sweep_blocks_per_sm(const LaunchConfig &c);
+// Grid that makes every block resident (grid == 0 resolved).
+int resolve_grid(const LaunchConfig &c, uint64_t L, uint64_t rows);
+cudaError_t launch_half_sweep(HalfSweepArgs a, const LaunchConfig &c, cudaStream_t s);
 
 // Hot start (Philox with counter word 2 = 0xFFFFFFFF), cold start is a memset.
 cudaError_t launch_init_hot(void *spins, uint64_t L, uint32_t word_bits, uint64_t seed,

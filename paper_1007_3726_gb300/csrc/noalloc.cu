@@ -10,6 +10,7 @@
 // (the per-sweep M/E counters) in a fixed array compiled into the library
 // instead of allocating it.
 #include "ising.h"
+#include "handle.h"
 #include "kernels.h"
 #include "runtime.h"
 
@@ -92,22 +93,13 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
     HalfSweepArgs a{};
     a.spins = d_spins;
     a.L = L;
-    a.words_per_row = (uint32_t)(L / word_bits);
-    a.rows_per_item = 8;
+    a.rows = L;
     a.key = make_round_keys(seed);
     a.thr4 = threshold_for(4.0, T);
     a.thr8 = threshold_for(8.0, T);
-    LaunchShape shape{1, 256};
-    {
-        int dev = 0, sms = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const uint64_t items = (L / a.rows_per_item) * a.words_per_row;
-        const uint64_t need = (items + shape.block - 1) / shape.block;
-        const uint64_t cap_blocks = (uint64_t)(sms > 0 ? sms : 1) *
-                                    half_sweep_blocks_per_sm(word_bits, shape.block);
-        shape.grid = (int)(need < cap_blocks ? need : cap_blocks);
-    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const LaunchConfig cfg = default_launch(dev, L, word_bits);
     uint64_t slot = 0;
     for (uint64_t i = 0; i < nsweeps && e == cudaSuccess; ++i) {
         const uint64_t t = t0 + i;
@@ -117,7 +109,7 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
             a.c3 = (stream_id << 1) | p;
             a.acc = (p == 1 && record_every && (t + 1) % record_every == 0) ? acc + 2 * (slot++)
                                                                           : nullptr;
-            e = launch_half_sweep(a, word_bits, shape, s);
+            e = launch_half_sweep(a, cfg, s);
         }
     }
     if (e == cudaSuccess && nrec) {

@@ -181,3 +181,64 @@ def test_large_lattice_L32768(P, orc):
     d = lat.measure()
     assert d["sweeps_done"] == 1000 and d["n_samples"] == 1000
     assert (d["M"], d["E"]) == lat.recount()
+
+
+def test_every_launch_configuration_is_bit_exact(P, orc):
+    """Processing width, register cap, block size, rows per item and grid change
+    only the speed: every candidate must reproduce the oracle bit for bit."""
+    L, T, seed, sid, n = 320, TC, 91, 2, 3
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_hot(L, seed, sid)
+    Mo, Eo = orc.run(s, n, seed, sid, thr4, thr8)
+    cands = P.ising_launch_candidates(L)
+    assert len(cands) >= 60
+    extra = [dict(cands[0], grid=1), dict(cands[-1], grid=3), dict(cands[5], grid=7)]
+    for cfg in cands + extra:
+        lat = P.Lattice(L, T, seed=seed, stream_id=sid, init="hot", word_bits=32)
+        lat.set_launch(**cfg)
+        M, E = lat.sweep(n, 1, collect=True)
+        assert np.array_equal(M, Mo) and np.array_equal(E, Eo), cfg
+        assert np.array_equal(lat.spins(), s), cfg
+        lat.close()
+
+
+def test_grid_stride_on_a_wider_lattice(P, orc):
+    L, T, seed, n = 2048, 2.2, 5, 4
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_hot(L, seed)
+    Mo, Eo = orc.run(s, n, seed, 0, thr4, thr8)
+    for cfg in ({"proc_bits": 32, "regcap": 0, "block": 128, "rows_per_item": 16, "grid": 5},
+                {"proc_bits": 64, "regcap": 2, "block": 512, "rows_per_item": 2, "grid": 0},
+                {"proc_bits": 64, "regcap": 1, "block": 256, "rows_per_item": 32, "grid": 152}):
+        lat = P.Lattice(L, T, seed=seed, init="hot", word_bits=64)
+        lat.set_launch(**cfg)
+        M, E = lat.sweep(n, 1, collect=True)
+        assert np.array_equal(M, Mo) and np.array_equal(E, Eo), cfg
+        assert np.array_equal(lat.spins(), s), cfg
+
+
+def test_autotune_keeps_the_lattice_and_the_results(P, orc):
+    L, T, seed = 1024, TC, 13
+    lat = P.Lattice(L, T, seed=seed, init="hot")
+    lat.sweep(2, 1)
+    before = lat.spins()
+    cfg, us = lat.autotune(reps=1)
+    assert cfg in P.ising_launch_candidates(L) and us > 0
+    assert lat.launch == cfg
+    assert np.array_equal(lat.spins(), before)
+    M, E = lat.sweep(3, 1, collect=True)
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_hot(L, seed)
+    Mo, Eo = orc.run(s, 5, seed, 0, thr4, thr8)
+    assert np.array_equal(M, Mo[2:]) and np.array_equal(E, Eo[2:])
+    assert np.array_equal(lat.spins(), s)
+    # a later handle of the same size starts from the tuned configuration
+    assert P.Lattice(L, 3.0, seed=1).launch == cfg
+
+
+def test_invalid_launch_configurations_are_rejected(P):
+    lat = P.Lattice(192, 2.0, seed=1)
+    for bad in ({"proc_bits": 48}, {"regcap": 3}, {"block": 96}, {"rows_per_item": 5},
+                {"rows_per_item": 128}, {"grid": 2 ** 24}):
+        with pytest.raises(P.IsingError):
+            lat.set_launch(**bad)
