@@ -175,9 +175,12 @@ ISING_API const char *ising_last_error(void);
  *   block          threads per block: 128, 256 or 512
  *   rows_per_item  rows one thread walks down per work item (divides L, <= 64)
  *   grid           blocks, 0 = as many as can be resident at once
+ *   insert         0, 1 or 2: how many of the two acceptance masks (u < thr4,
+ *                  u < thr8) are built with logic operations rather than
+ *                  additions (a balance between two integer pipelines)
  */
 typedef struct {
-    uint32_t proc_bits, regcap, block, rows_per_item, grid;
+    uint32_t proc_bits, regcap, block, rows_per_item, grid, insert;
 } ising_launch;
 
 /* The handle's current configuration. */

@@ -20,17 +20,27 @@ def main(argv=None):
     ap.add_argument("--record-every", type=int, default=1)
     ap.add_argument("--word-bits", type=int, default=0)
     ap.add_argument("--time", action="store_true", help="report wall time of the sweeps")
+    ap.add_argument("--autotune", action="store_true", help="pick the launch configuration first")
+    ap.add_argument("--launch", default=None,
+                    help="launch configuration proc_bits,regcap,block,rows_per_item[,grid[,insert]]")
     a = ap.parse_args(argv)
 
     import paper_1007_3726_gb300 as P
 
     P.load()
     lat = P.Lattice(a.L, a.T, seed=a.seed, stream_id=a.stream_id, init=a.init, word_bits=a.word_bits)
+    if a.autotune:
+        cfg, _ = lat.autotune()
+    if a.launch:
+        v = [int(x) for x in a.launch.split(",")]
+        keys = ["proc_bits", "regcap", "block", "rows_per_item", "grid", "insert"]
+        lat.set_launch(**dict(zip(keys, v)))
     t0 = time.perf_counter()
     lat.sweep(a.sweeps, a.record_every)
     d = lat.measure()
     el = time.perf_counter() - t0
     d["L"], d["T"], d["word_bits"] = a.L, a.T, lat.word_bits
+    d["launch"] = lat.launch
     if a.time:
         d["seconds"] = el
         d["attempts_per_ns"] = a.L * a.L * a.sweeps / el / 1e9

@@ -24,11 +24,11 @@ std::map<std::tuple<int, uint64_t, uint32_t>, LaunchConfig> g_tuned;
 
 ising_launch to_abi(const LaunchConfig &c)
 {
-    return ising_launch{c.proc_bits, c.regcap, c.block, c.rows_per_item, c.grid};
+    return ising_launch{c.proc_bits, c.regcap, c.block, c.rows_per_item, c.grid, c.insert};
 }
 LaunchConfig from_abi(const ising_launch &l)
 {
-    return LaunchConfig{l.proc_bits, l.regcap, l.block, l.rows_per_item, l.grid};
+    return LaunchConfig{l.proc_bits, l.regcap, l.insert, l.block, l.rows_per_item, l.grid};
 }
 }  // namespace
 
@@ -41,7 +41,7 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
         auto it = g_tuned.find(std::make_tuple(device, L, word_bits));
         if (it != g_tuned.end()) return it->second;
     }
-    LaunchConfig c{64, 0, 256, 8, 0};
+    LaunchConfig c{64, 1, 1, 512, 8, 0};
     return c;
 }
 
@@ -56,11 +56,12 @@ std::vector<LaunchConfig> launch_candidates(uint64_t L, uint64_t rows)
     std::vector<LaunchConfig> out;
     for (uint32_t pb : {32u, 64u})
         for (uint32_t rc : {0u, 1u, 2u})
-            for (uint32_t blk : {128u, 256u, 512u})
-                for (uint32_t R : {2u, 4u, 8u, 16u, 32u}) {
-                    LaunchConfig c{pb, rc, blk, R, 0};
-                    if (launch_config_valid(c, L, rows)) out.push_back(c);
-                }
+            for (uint32_t ins : {0u, 1u, 2u})
+                for (uint32_t blk : {128u, 256u, 512u})
+                    for (uint32_t R : {4u, 8u, 16u}) {
+                        LaunchConfig c{pb, rc, ins, blk, R, 0};
+                        if (launch_config_valid(c, L, rows)) out.push_back(c);
+                    }
     return out;
 }
 
@@ -147,9 +148,9 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
         float ms = 0;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e == cudaSuccess && log)
-            std::fprintf(stderr, "autotune L=%llu rows=%llu proc_bits=%u regcap=%u block=%u R=%u: %.2f us/step\n",
+            std::fprintf(stderr, "autotune L=%llu rows=%llu proc_bits=%u regcap=%u insert=%u block=%u R=%u: %.2f us/step\n",
                          (unsigned long long)h->L, (unsigned long long)rows, c.proc_bits, c.regcap,
-                         c.block, c.rows_per_item, 1e3 * ms / (2.0 * reps));
+                         c.insert, c.block, c.rows_per_item, 1e3 * ms / (2.0 * reps));
         if (e == cudaSuccess && ms < best_ms) {
             best_ms = ms;
             best_c = c;

@@ -107,10 +107,14 @@ __device__ __forceinline__ void block_accumulate(unsigned int a, unsigned int b,
     }
 }
 
-// The acceptance masks of one word: bit 8q + 2l of half (q / 4) is set when
-// draw l of the word's Philox call q is below the threshold.  Round 1 and the
-// word-0/word-3 half of round 2 are taken from the step-uniform values.
-template <int NB>
+// The acceptance masks of one word whose first Philox group is g0: bit
+// 8q + 2l of half (q / 4) is set when draw l of the word's call q is below the
+// threshold.  Round 1 and the word-0/word-3 half of round 2 come from the
+// step-uniform values; the round-1 products A * (g0 + q) are one widening
+// multiply per word plus 64-bit additions of the constants A * q (the low
+// counter words g0 .. g0 + NB - 1 of a word never wrap, since g0 is a
+// multiple of NB).
+template <int NB, int INS>
 __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t g0,
                                                 uint32_t (&p4)[(NB + 3) / 4],
                                                 uint32_t (&p8)[(NB + 3) / 4])
@@ -122,16 +126,19 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
         r2x2k = (uint32_t)(pa >> 32) ^ a.key.k1[1];
         r2x3 = (uint32_t)pa;
     }
-    const uint32_t glo = (uint32_t)g0;
+    const uint64_t pa0 = (uint64_t)(uint32_t)g0 * kPhiloxMulA;
+    // INS >= 1 (>= 2) starts the P4 (P8) mask from a zero the compiler cannot
+    // see, so that its bit insertions stay ORs on the ALU pipe instead of
+    // becoming additions on the pipe that also carries the Philox multiplies.
 #pragma unroll
     for (int h = 0; h < (NB + 3) / 4; ++h) {
-        p4[h] = 0u;
-        p8[h] = 0u;
+        p4[h] = INS >= 1 ? a.zero : 0u;
+        p8[h] = INS >= 2 ? a.zero : 0u;
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
         // round 1: words 0, 1 are uniform (r1x0 ^ c1, lo(B t))
-        const uint64_t pa = (uint64_t)(glo + (uint32_t)q) * kPhiloxMulA;
+        const uint64_t pa = pa0 + (uint64_t)kPhiloxMulA * (uint64_t)q;
         const uint32_t x2 = (uint32_t)(pa >> 32) ^ a.r1x2k;
         const uint32_t x3 = (uint32_t)pa;
         // round 2: the product A * word 0 is uniform per word
@@ -158,42 +165,45 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
 
 // One checkerboard step.  Work item = (block of R rows, word column w); the
 // thread walks down its column keeping the rows above / at / below in
-// registers.  Rows it reads but does not own (the halo rows and the adjacent
+// registers, advancing its row pointers, group index and parity mask by
+// additions.  Rows it reads but does not own (the halo rows and the adjacent
 // words) are only used at bit positions of the other parity, which no thread
 // writes during this step.
-template <typename Word>
+template <typename Word, int INS>
 __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
 {
     using Tr = WordTraits<Word>;
     constexpr int B = Tr::bits;
     constexpr int NB = B / 8;  // Philox calls (bytes) per word
-    Word *S = static_cast<Word *>(a.spins);
+    Word *const S = static_cast<Word *>(a.spins);
     const uint64_t rows = a.rows;
     const uint32_t W = a.words_per_row;
     const uint32_t R = a.rows_per_item;
     const uint32_t nrb = (uint32_t)(rows / R);
     const uint64_t groups_per_row = a.L >> 3;
+    const Word even = Tr::even;
 
     unsigned int cnt_up = 0, cnt_anti = 0;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t rb = tid / W;
     uint32_t w = tid - rb * W;
     while (rb < nrb) {
-        const uint32_t wl = (w == 0) ? W - 1 : w - 1;
-        const uint32_t wr = (w + 1 == W) ? 0 : w + 1;
+        const int64_t dl = (w == 0) ? (int64_t)W - 1 : -1;  // to the left neighbour word
+        const int64_t dr = (w + 1 == W) ? 1 - (int64_t)W : 1;
         const uint64_t y0 = (uint64_t)rb * R;
-        Word up = S[((y0 == 0) ? rows - 1 : y0 - 1) * W + w];
-        Word cur = S[y0 * W + w];
+        Word *p = S + y0 * W + w;
+        Word up = *((y0 == 0) ? S + (rows - 1) * W + w : p - W);
+        Word cur = *p;
+        uint64_t g = y0 * groups_per_row + (uint64_t)w * NB;
+        uint32_t off = (uint32_t)((y0 + a.p) & 1u);  // parity of the target bit positions
         for (uint32_t r = 0; r < R; ++r) {
-            const uint64_t y = y0 + r;
-            const uint64_t yd = (y + 1 == rows) ? 0 : y + 1;
-            const Word dn = S[yd * W + w];
-            const Word lw = S[y * W + wl];
-            const Word rw = S[y * W + wr];
+            Word *const pn = (y0 + r + 1 == rows) ? S + w : p + W;
+            const Word dn = *pn;
+            const Word lw = p[dl];
+            const Word rw = p[dr];
             const Word left = (cur << 1) | (lw >> (B - 1));   // bit b holds s(x - 1)
             const Word right = (cur >> 1) | (rw << (B - 1));  // bit b holds s(x + 1)
-            const uint32_t off = (uint32_t)((y + a.p) & 1u);  // parity of target bit positions
-            const Word mask = off ? (Word)(Tr::even << 1) : Tr::even;
+            const Word mask = off ? (Word)(even << 1) : even;
 
             // energy variables and their bit-sliced sum c = i1 + i2 + i3 + i4
             const Word i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
@@ -206,12 +216,12 @@ __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
 
             // the sites' draws: byte q of the word holds four target sites
             uint32_t h4[(NB + 3) / 4], h8[(NB + 3) / 4];
-            word_draw_masks<NB>(a, y * groups_per_row + (uint64_t)w * NB, h4, h8);
+            word_draw_masks<NB, INS>(a, g, h4, h8);
             const Word p4 = Tr::from_halves(h4) << off;
             const Word p8 = Tr::from_halves(h8) << off;
             const Word flip = mask & (ge2 | (eq1 & p4) | (eq0 & p8));
             const Word nw = cur ^ flip;
-            S[y * W + w] = nw;
+            *p = nw;
             if (a.acc) {
                 // after the step: +1 spins of the word, and the anti-aligned
                 // bonds of its target sites (their neighbours are final)
@@ -221,6 +231,9 @@ __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
             }
             up = nw;
             cur = dn;
+            p = pn;
+            g += groups_per_row;
+            off ^= 1u;
         }
         rb += a.stride_rb;
         w += a.stride_w;
@@ -232,20 +245,20 @@ __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
     if (a.acc) block_accumulate(cnt_up, cnt_anti, a.acc);
 }
 
-template <typename Word>
+template <typename Word, int INS>
 __global__ void __launch_bounds__(512) k_half_sweep(const __grid_constant__ HalfSweepArgs a)
 {
-    half_sweep_body<Word>(a);
+    half_sweep_body<Word, INS>(a);
 }
-template <typename Word>
+template <typename Word, int INS>
 __global__ void __launch_bounds__(512, 3) k_half_sweep_r40(const __grid_constant__ HalfSweepArgs a)
 {
-    half_sweep_body<Word>(a);
+    half_sweep_body<Word, INS>(a);
 }
-template <typename Word>
+template <typename Word, int INS>
 __global__ void __launch_bounds__(512, 4) k_half_sweep_r32(const __grid_constant__ HalfSweepArgs a)
 {
-    half_sweep_body<Word>(a);
+    half_sweep_body<Word, INS>(a);
 }
 
 template <typename Word>
@@ -361,16 +374,25 @@ RoundKeys make_round_keys(uint64_t seed)
 namespace {
 using HalfSweepKernel = void (*)(HalfSweepArgs);
 
+template <typename Word, int INS>
+HalfSweepKernel pick_regcap(uint32_t regcap)
+{
+    if (regcap == 1) return k_half_sweep_r40<Word, INS>;
+    if (regcap == 2) return k_half_sweep_r32<Word, INS>;
+    return k_half_sweep<Word, INS>;
+}
+
+template <typename Word>
+HalfSweepKernel pick_ins(const LaunchConfig &c)
+{
+    if (c.insert == 1) return pick_regcap<Word, 1>(c.regcap);
+    if (c.insert == 2) return pick_regcap<Word, 2>(c.regcap);
+    return pick_regcap<Word, 0>(c.regcap);
+}
+
 HalfSweepKernel half_sweep_kernel(const LaunchConfig &c)
 {
-    if (c.proc_bits == 64) {
-        if (c.regcap == 1) return k_half_sweep_r40<uint64_t>;
-        if (c.regcap == 2) return k_half_sweep_r32<uint64_t>;
-        return k_half_sweep<uint64_t>;
-    }
-    if (c.regcap == 1) return k_half_sweep_r40<uint32_t>;
-    if (c.regcap == 2) return k_half_sweep_r32<uint32_t>;
-    return k_half_sweep<uint32_t>;
+    return c.proc_bits == 64 ? pick_ins<uint64_t>(c) : pick_ins<uint32_t>(c);
 }
 
 uint64_t mulA(uint32_t x) { return (uint64_t)x * kPhiloxMulA; }
@@ -395,6 +417,7 @@ bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
     if (c.proc_bits != 32 && c.proc_bits != 64) return false;
     if (c.regcap > 2) return false;
+    if (c.insert > 2) return false;
     if (c.block != 128 && c.block != 256 && c.block != 512) return false;
     if (c.rows_per_item < 1 || c.rows_per_item > 64 || rows % c.rows_per_item != 0) return false;
     if (L % c.proc_bits != 0) return false;
@@ -427,6 +450,7 @@ cudaError_t launch_half_sweep(HalfSweepArgs a, const LaunchConfig &c, cudaStream
     const int grid = resolve_grid(c, a.L, a.rows);
     a.words_per_row = (uint32_t)(a.L / c.proc_bits);
     a.rows_per_item = c.rows_per_item;
+    a.zero = 0u;
     prepare_half_sweep(a, grid, (int)c.block);
     half_sweep_kernel(c)<<<grid, c.block, 0, s>>>(a);
     return cudaGetLastError();

@@ -36,6 +36,7 @@ struct HalfSweepArgs {
     uint32_t r2x0k;  // lo(B t) ^ k0[1]
     uint32_t r2x2k;  // hi(A r1x0) ^ k1[1]   (counter word 1 == 0)
     uint32_t r2x3;   // lo(A r1x0)           (counter word 1 == 0)
+    uint32_t zero;   // 0, passed at run time (see word_draw_masks)
     // grid-stride walk over items (item = row block * words_per_row + word)
     uint32_t stride_rb, stride_w;  // (grid * block) / words_per_row, (grid * block) % words_per_row
     // If not null (step B only): acc[0] += number of +1 spins of the whole
@@ -53,6 +54,7 @@ void prepare_half_sweep(HalfSweepArgs &a, int grid, int block);
 struct LaunchConfig {
     uint32_t proc_bits;      // 32 or 64: bits one thread updates per row
     uint32_t regcap;         // 0: compiler's choice, 1: <= 40 registers, 2: <= 32 registers
+    uint32_t insert;         // acceptance-bit insertion kept on the ALU pipe: 0 none, 1 P4, 2 P4+P8
     uint32_t block;          // 128, 256 or 512 threads
     uint32_t rows_per_item;  // 2 .. 64, divides L
     uint32_t grid;           // blocks (0 = all resident blocks of the device)
