@@ -200,6 +200,58 @@ ISING_API uint32_t ising_launch_candidates(uint64_t L, ising_launch *out, uint32
 ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_launch *best,
                                       double *best_us_per_step);
 
+/* ---- many lattices in one persistent launch ----------------------------- */
+
+/*
+ * A batch runs many lattices of uneven size in one persistent, cooperative
+ * kernel launch.  Each lattice is cut into strips of rows held in shared
+ * memory for the whole launch; strips of one lattice on different CTAs swap
+ * their boundary rows after every checkerboard step through border arrays in
+ * global memory (the border exchange of Sec. 6.1, between CTAs of one GPU),
+ * and each strip waits only for its two neighbours.  Lattices, samples and
+ * final states are bit-identical to ising_sweep on each handle: the batch
+ * changes where and when sites are updated, never how.
+ *
+ * Options (zero = default):
+ *   block          threads per CTA, 256 or 512 (512)
+ *   ctas_per_sm    resident CTAs per SM the plan is made for (2); each CTA gets
+ *                  that share of the SM's shared memory
+ *   rows_per_item  rows one thread walks per item (4)
+ *   insert         as in ising_launch (0)
+ *   use_graph      1: capture one run in a CUDA graph on the first run and
+ *                  replay it afterwards
+ *   wait_ms        limit of one wait for a neighbour strip (2000 ms); when it
+ *                  runs out the launch stops, ising_batch_run returns
+ *                  ISING_ERR_TIMEOUT and the handles become failed
+ *   hold_strip     failure-detection testing only: 1 + index of a strip that
+ *                  never announces its steps, so that its neighbours' waits
+ *                  run out (0 = none)
+ */
+typedef struct ising_batch ising_batch;
+typedef struct {
+    uint32_t block, ctas_per_sm, rows_per_item, insert, use_graph;
+    double wait_ms;
+    uint32_t hold_strip;
+} ising_batch_opts;
+
+/* Plans a batch of n distinct handles on one device; each run advances handle
+ * i by nsweeps[i] sweeps (1 .. 2^30) and records samples every record_every
+ * sweeps as ising_sweep does.  ISING_ERR_INVALID if the lattices do not fit in
+ * the GPU's shared memory at once.  The handles must outlive the batch. */
+ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
+                                          uint32_t record_every, const ising_batch_opts *opts,
+                                          ising_batch **out);
+/* Performs `runs` runs one after another (one launch each); waits for the GPU
+ * after each and appends the samples to the handles. */
+ISING_API ising_status ising_batch_run(ising_batch *b, uint32_t runs);
+/* CTAs, threads per CTA, strips and dynamic shared memory of the plan. */
+ISING_API ising_status ising_batch_info(const ising_batch *b, uint32_t *grid, uint32_t *block,
+                                        uint32_t *strips, size_t *smem_bytes);
+ISING_API ising_status ising_batch_destroy(ising_batch *b);
+/* One run of a batch made with default options, then destroyed. */
+ISING_API ising_status ising_sweep_batch(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
+                                         uint32_t record_every);
+
 /*
  * ising_sweep_noalloc - the sweep for callers that cannot allocate memory.
  * The paper has no counterpart; this entry point exists for callers that own

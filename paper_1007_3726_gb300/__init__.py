@@ -23,7 +23,8 @@ __all__ = [
     "ising_measure", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
     "ising_device_spins", "ising_sweep_noalloc", "ising_get_launch", "ising_set_launch",
-    "ising_launch_candidates", "ising_autotune", "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
+    "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "Batch", "IsingBatchOpts",
+    "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
@@ -63,6 +64,13 @@ class IsingLaunch(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IsingBatchOpts(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("rows_per_item", ctypes.c_uint32), ("insert", ctypes.c_uint32),
+                ("use_graph", ctypes.c_uint32), ("wait_ms", ctypes.c_double),
+                ("hold_strip", ctypes.c_uint32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -105,6 +113,12 @@ def load(path: str | None = None):
                                     ctypes.c_uint32),
         "ising_autotune": ([H, ctypes.c_uint32, ctypes.POINTER(IsingLaunch),
                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "ising_batch_create": ([ctypes.POINTER(H), ctypes.c_uint32, _u64p, ctypes.c_uint32,
+                                ctypes.POINTER(IsingBatchOpts), ctypes.POINTER(H)], ctypes.c_int),
+        "ising_batch_run": ([H, ctypes.c_uint32], ctypes.c_int),
+        "ising_batch_info": ([H, _u32p, _u32p, _u32p, _szp], ctypes.c_int),
+        "ising_batch_destroy": ([H], ctypes.c_int),
+        "ising_sweep_batch": ([ctypes.POINTER(H), ctypes.c_uint32, _u64p, ctypes.c_uint32], ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
@@ -228,6 +242,61 @@ def ising_autotune(h, reps: int = 3) -> tuple[dict, float]:
     us = ctypes.c_double()
     _check(load().ising_autotune(h, reps, ctypes.byref(o), ctypes.byref(us)))
     return o.as_dict(), us.value
+
+
+def _handles(lats):
+    hs = [(l.handle if isinstance(l, Lattice) else l) for l in lats]
+    return (ctypes.c_void_p * len(hs))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
+
+
+def ising_sweep_batch(lats, nsweeps, record_every: int = 0):
+    """One persistent launch over many lattices (handles or Lattice objects)."""
+    arr = _handles(lats)
+    ns = (ctypes.c_uint64 * len(lats))(*[int(x) for x in nsweeps])
+    _check(load().ising_sweep_batch(arr, len(lats), ns, record_every))
+
+
+class Batch:
+    """A planned persistent multi-lattice launch (ising_batch_create / _run)."""
+
+    def __init__(self, lats, nsweeps, record_every: int = 0, block: int = 0, ctas_per_sm: int = 0,
+                 rows_per_item: int = 0, insert: int = 0, use_graph: bool = False,
+                 wait_ms: float = 0.0, hold_strip: int = 0):
+        self._lats = list(lats)  # keep the handles alive
+        arr = _handles(self._lats)
+        ns = (ctypes.c_uint64 * len(self._lats))(*[int(x) for x in nsweeps])
+        o = IsingBatchOpts(block=block, ctas_per_sm=ctas_per_sm, rows_per_item=rows_per_item,
+                           insert=insert, use_graph=1 if use_graph else 0, wait_ms=wait_ms,
+                           hold_strip=hold_strip)
+        self._b = ctypes.c_void_p()
+        _check(load().ising_batch_create(arr, len(self._lats), ns, record_every, ctypes.byref(o),
+                                         ctypes.byref(self._b)))
+
+    def run(self, runs: int = 1):
+        _check(load().ising_batch_run(self._b, runs))
+
+    def info(self) -> dict:
+        g, b, st, sm = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_size_t()
+        _check(load().ising_batch_info(self._b, ctypes.byref(g), ctypes.byref(b), ctypes.byref(st),
+                                       ctypes.byref(sm)))
+        return {"grid": g.value, "block": b.value, "strips": st.value, "smem_bytes": sm.value}
+
+    def close(self):
+        if self._b is not None and self._b.value:
+            load().ising_batch_destroy(self._b)
+        self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 _alloc_keepalive = []

@@ -1,0 +1,845 @@
+// Persistent multi-lattice sweep: many lattices of uneven size in one launch.
+//
+// Each lattice is cut into strips of rows; every CTA keeps its strips in
+// shared memory for the whole launch and walks through the checkerboard steps
+// (Sec. 3) of all of them.  A strip needs its neighbours' boundary rows before
+// each step: a lattice held by one strip wraps around inside the CTA; strips
+// of a lattice spread over several CTAs exchange their boundary rows through
+// small border arrays in global memory (the own / neighbour border arrays of
+// the paper's multi-GPU scheme, Sec. 6.1, here between CTAs of one GPU), and a
+// strip waits only until its two neighbours have published the previous step
+// (a point-to-point dependency, not a global barrier).  All CTAs are resident
+// at once (cooperative launch), every wait has a clock limit after which the
+// launch sets an error flag and returns.  The arithmetic of a site update is
+// the same device code as the one-lattice kernel, so every lattice, sample and
+// final state is bit-identical to ising_sweep's.
+#include "handle.h"
+#include "kernels.h"
+#include "runtime.h"
+#include "sweep_device.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace ising;
+
+namespace ising {
+
+// One strip of one lattice (device-visible plan entry).
+struct BatchStrip {
+    uint64_t *lat;                      // the lattice, rows of W 64-bit words
+    uint64_t *border;                   // [2 buffers][top, bottom][W] words (multi-strip only)
+    unsigned int *progress;             // steps this strip has completed (multi-strip only)
+    unsigned long long *samples;        // the lattice's recorded counters [n][2]
+    unsigned long long *final_counts;   // the lattice's counters after its last sweep [2]
+    uint64_t L;
+    uint32_t W;                         // 64-bit words per row
+    uint32_t row0, nrows;               // the strip's rows
+    uint32_t up_strip, dn_strip;        // plan indices of the neighbouring strips
+    uint32_t nstrips_lat;               // strips of this lattice
+    uint32_t smem_off;                  // first word of the strip's buffer in shared memory
+    uint32_t lat_index;                 // lattice index in the batch
+    uint32_t nsteps;                    // 2 x sweeps of this launch
+    uint32_t record_every;
+    uint32_t thr4, thr8, c3base;        // thresholds, stream_id << 1
+    RoundKeys key;
+};
+
+struct BatchLaunchArgs {
+    const BatchStrip *strips;
+    const uint32_t *cta_first;          // strips of CTA b: cta_strips[cta_first[b] .. cta_first[b + 1])
+    const uint32_t *cta_strips;
+    const uint32_t *t0;                 // first sweep index of each lattice in this launch
+    uint32_t max_steps;
+    uint32_t rows_per_item;
+    unsigned int *error_flag;           // set to 1 when a wait ran out
+    long long wait_cycles;              // clock limit of one wait
+    uint32_t hold_strip;                // 1 + index of a strip that never publishes (0 = none)
+};
+
+namespace {
+
+constexpr uint32_t kFlagTimeout = 1u;
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_release(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits (bounded) until the neighbours of every multi-strip strip of
+// this CTA have completed `need` steps; the result is broadcast to the CTA.
+// Returns false when a wait ran out or another CTA reported a failure.
+__device__ bool wait_neighbours(const BatchLaunchArgs &A, uint32_t first, uint32_t last, uint32_t s)
+{
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        int good = 1;
+        const long long start = clock64();
+        for (uint32_t j = first; j < last && good; ++j) {
+            const BatchStrip &st = A.strips[A.cta_strips[j]];
+            if (st.nstrips_lat == 1 || s >= st.nsteps) continue;
+            const unsigned int *pu = A.strips[st.up_strip].progress;
+            const unsigned int *pd = A.strips[st.dn_strip].progress;
+            unsigned int ns = 32;
+            while (!(load_acquire(pu) >= s && load_acquire(pd) >= s)) {
+                if (*(volatile unsigned int *)A.error_flag != 0u || clock64() - start > A.wait_cycles) {
+                    atomicOr(A.error_flag, kFlagTimeout);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+            }
+        }
+        ok = good;
+    }
+    __syncthreads();
+    const bool r = ok != 0;
+    __syncthreads();
+    return r;
+}
+
+// Step-uniform Philox values of (t, p) for a strip (cf. prepare_half_sweep).
+__device__ __forceinline__ void strip_step_args(HalfSweepArgs &a, const BatchStrip &st, uint32_t t,
+                                                uint32_t p)
+{
+    a.key = st.key;
+    a.thr4 = st.thr4;
+    a.thr8 = st.thr8;
+    a.t = t;
+    a.p = p;
+    a.c3 = st.c3base | p;
+    const uint64_t pb = (uint64_t)t * kPhiloxMulB;
+    a.r1x0 = (uint32_t)(pb >> 32) ^ st.key.k0[0];
+    a.r1x2k = a.c3 ^ st.key.k1[0];
+    a.r2x0k = (uint32_t)pb ^ st.key.k0[1];
+    const uint64_t pa = (uint64_t)a.r1x0 * kPhiloxMulA;
+    a.r2x2k = (uint32_t)(pa >> 32) ^ st.key.k1[1];
+    a.r2x3 = (uint32_t)pa;
+    a.zero = 0u;
+}
+
+constexpr uint32_t kMaxStripsPerCta = 64;
+
+// Each step has four phases: wait for the neighbour strips of the previous
+// step, fill the halo rows of all strips, update all strips (one flat loop
+// over the (strip, row block, word) items of the CTA, so that small lattices
+// share the CTA's threads), then add the counters and publish the boundary
+// rows.
+template <int INS>
+__global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchLaunchArgs A)
+{
+    extern __shared__ uint64_t sm[];
+    __shared__ uint32_t item_end[kMaxStripsPerCta];   // prefix sums of the strips' items
+    __shared__ uint32_t strip_R[kMaxStripsPerCta];    // rows per item of each strip
+    __shared__ unsigned int cnt[kMaxStripsPerCta][2];  // step counters of each strip
+    __shared__ HalfSweepArgs sargs[kMaxStripsPerCta];  // step arguments of each strip
+    __shared__ uint8_t scount[kMaxStripsPerCta];       // does the strip count in this step
+    const uint32_t first = A.cta_first[blockIdx.x], last = A.cta_first[blockIdx.x + 1];
+    const uint32_t ns = last - first;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+
+    // the strips' rows into shared memory (row r of a strip at buffer row r + 1)
+    for (uint32_t j = first; j < last; ++j) {
+        const BatchStrip &st = A.strips[A.cta_strips[j]];
+        const uint64_t n = (uint64_t)st.nrows * st.W;
+        const uint64_t *src = st.lat + (uint64_t)st.row0 * st.W;
+        uint64_t *dst = sm + st.smem_off + st.W;
+        for (uint64_t i = tid; i < n; i += nthr) dst[i] = src[i];
+    }
+    if (tid == 0) {
+        for (uint32_t k = 0; k < ns; ++k) {
+            const BatchStrip &st = A.strips[A.cta_strips[first + k]];
+            // enough items for every thread when the strip is small
+            uint32_t R = A.rows_per_item;
+            while (R > 1 && (uint64_t)((st.nrows + R - 1) / R) * st.W < nthr) R >>= 1;
+            strip_R[k] = R;
+        }
+    }
+    __syncthreads();
+
+    for (uint32_t s = 0; s < A.max_steps; ++s) {
+        const uint32_t p = s & 1u;
+        // 1. neighbours of the previous step
+        if (s > 0 && !wait_neighbours(A, first, last, s)) return;
+        // 2. halo rows, and the item ranges of this step
+        for (uint32_t k = 0; k < ns; ++k) {
+            const BatchStrip &st = A.strips[A.cta_strips[first + k]];
+            if (s >= st.nsteps) continue;
+            const uint32_t W = st.W, nrows = st.nrows;
+            uint64_t *buf = sm + st.smem_off;
+            if (st.nstrips_lat == 1) {
+                for (uint32_t i = tid; i < W; i += nthr) {
+                    buf[i] = buf[(uint64_t)nrows * W + i];              // row nrows-1 above row 0
+                    buf[(uint64_t)(nrows + 1) * W + i] = buf[W + i];    // row 0 below row nrows-1
+                }
+            } else if (s == 0) {
+                const uint64_t ya = (st.row0 == 0) ? st.L - 1 : st.row0 - 1;
+                const uint64_t yb = (st.row0 + nrows == st.L) ? 0 : st.row0 + nrows;
+                for (uint32_t i = tid; i < W; i += nthr) {
+                    buf[i] = __ldcg(st.lat + ya * W + i);
+                    buf[(uint64_t)(nrows + 1) * W + i] = __ldcg(st.lat + yb * W + i);
+                }
+            } else {
+                const uint32_t pb = (s - 1) & 1u;
+                const uint64_t *bu = A.strips[st.up_strip].border + (uint64_t)(2 * pb + 1) * W;  // its bottom row
+                const uint64_t *bd = A.strips[st.dn_strip].border + (uint64_t)(2 * pb + 0) * W;  // its top row
+                for (uint32_t i = tid; i < W; i += nthr) {
+                    buf[i] = __ldcg(bu + i);
+                    buf[(uint64_t)(nrows + 1) * W + i] = __ldcg(bd + i);
+                }
+            }
+        }
+        if (tid < ns) {
+            const BatchStrip &st = A.strips[A.cta_strips[first + tid]];
+            if (s < st.nsteps) {
+                const uint32_t t = A.t0[st.lat_index] + (s >> 1);
+                HalfSweepArgs a;
+                strip_step_args(a, st, t, p);
+                sargs[tid] = a;
+                const bool recorded = p == 1u && st.record_every != 0u && (t + 1) % st.record_every == 0u;
+                scount[tid] = (p == 1u && (recorded || s + 1 == st.nsteps)) ? 1 : 0;
+            }
+            cnt[tid][0] = 0u;
+            cnt[tid][1] = 0u;
+        }
+        if (tid == 0) {
+            uint32_t acc = 0;
+            for (uint32_t k = 0; k < ns; ++k) {
+                const BatchStrip &st = A.strips[A.cta_strips[first + k]];
+                if (s < st.nsteps) acc += ((st.nrows + strip_R[k] - 1) / strip_R[k]) * st.W;
+                item_end[k] = acc;
+            }
+        }
+        __syncthreads();
+
+        // 3. the updates
+        const uint32_t total = ns ? item_end[ns - 1] : 0u;
+        uint32_t k = 0, kbase = 0;
+        uint32_t kc = 0xFFFFFFFFu;  // the strip whose counts cu / ca hold
+        bool count = false;
+        unsigned int cu = 0, ca = 0;
+        for (uint32_t item = tid; item < total; item += nthr) {
+            while (item >= item_end[k]) {
+                kbase = item_end[k];
+                ++k;
+            }
+            const BatchStrip &st = A.strips[A.cta_strips[first + k]];
+            if (k != kc) {
+                if (count && (cu | ca)) {
+                    atomicAdd(&cnt[kc][0], cu);
+                    atomicAdd(&cnt[kc][1], ca);
+                }
+                cu = ca = 0;
+                kc = k;
+                count = scount[k] != 0;
+            }
+            const HalfSweepArgs &a = sargs[k];
+            const uint32_t W = st.W, R = strip_R[k];
+            const uint32_t li = item - kbase;
+            const uint32_t rb = li / W, w = li - rb * W;
+            const uint32_t wl = (w == 0) ? W - 1 : w - 1;
+            const uint32_t wr = (w + 1 == W) ? 0 : w + 1;
+            const uint32_t r0 = rb * R, r1 = min(r0 + R, st.nrows);
+            uint64_t *row = sm + st.smem_off + (uint64_t)(r0 + 1) * W;
+            uint64_t up = row[w - (uint64_t)W];
+            uint64_t cur = row[w];
+            const uint64_t groups_per_row = st.L >> 3;
+            const uint64_t y0 = (uint64_t)st.row0 + r0;
+            uint64_t g = y0 * groups_per_row + (uint64_t)w * 8u;
+            uint32_t off = (uint32_t)((y0 + p) & 1u);
+            for (uint32_t r = r0; r < r1; ++r) {
+                const uint64_t dn = row[W + w];
+                const uint64_t nw = update_word<uint64_t, INS>(a, cur, up, dn, row[wl], row[wr], off, g,
+                                                               count, cu, ca);
+                row[w] = nw;
+                up = nw;
+                cur = dn;
+                row += W;
+                g += groups_per_row;
+                off ^= 1u;
+            }
+        }
+        if (count && (cu | ca)) {
+            atomicAdd(&cnt[kc][0], cu);
+            atomicAdd(&cnt[kc][1], ca);
+        }
+        __syncthreads();
+
+        // 4. counters to the lattices' slots, boundary rows to the neighbours
+        if (tid < ns) {
+            const BatchStrip &st = A.strips[A.cta_strips[first + tid]];
+            if (s < st.nsteps && p == 1u) {
+                const uint32_t t = A.t0[st.lat_index] + (s >> 1);
+                const bool recorded = st.record_every != 0u && (t + 1) % st.record_every == 0u;
+                if (recorded) {
+                    const uint32_t slot = (t + 1) / st.record_every - A.t0[st.lat_index] / st.record_every - 1;
+                    atomicAdd(st.samples + 2 * slot, (unsigned long long)cnt[tid][0]);
+                    atomicAdd(st.samples + 2 * slot + 1, (unsigned long long)cnt[tid][1]);
+                }
+                if (s + 1 == st.nsteps) {
+                    atomicAdd(st.final_counts, (unsigned long long)cnt[tid][0]);
+                    atomicAdd(st.final_counts + 1, (unsigned long long)cnt[tid][1]);
+                }
+            }
+        }
+        bool any_multi = false;
+        for (uint32_t kk = 0; kk < ns; ++kk) {
+            const uint32_t si = A.cta_strips[first + kk];
+            const BatchStrip &st = A.strips[si];
+            if (st.nstrips_lat == 1 || s >= st.nsteps) continue;
+            any_multi = true;
+            const uint32_t W = st.W, nrows = st.nrows;
+            const uint64_t *buf = sm + st.smem_off;
+            uint64_t *bo = st.border + (uint64_t)(2 * p) * W;
+            for (uint32_t i = tid; i < W; i += nthr) {
+                __stcg(bo + i, buf[W + i]);                           // top row
+                __stcg(bo + W + i, buf[(uint64_t)nrows * W + i]);     // bottom row
+            }
+        }
+        if (any_multi) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                for (uint32_t kk = 0; kk < ns; ++kk) {
+                    const uint32_t si = A.cta_strips[first + kk];
+                    const BatchStrip &st = A.strips[si];
+                    if (st.nstrips_lat == 1 || s >= st.nsteps || A.hold_strip == si + 1) continue;
+                    store_release(st.progress, s + 1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // the strips back to the lattices
+    for (uint32_t j = first; j < last; ++j) {
+        const BatchStrip &st = A.strips[A.cta_strips[j]];
+        const uint64_t n = (uint64_t)st.nrows * st.W;
+        uint64_t *dst = st.lat + (uint64_t)st.row0 * st.W;
+        const uint64_t *src = sm + st.smem_off + st.W;
+        for (uint64_t i = tid; i < n; i += nthr) dst[i] = src[i];
+    }
+}
+
+}  // namespace
+}  // namespace ising
+
+namespace {
+using namespace ising;
+using BatchKernel = void (*)(BatchLaunchArgs);
+BatchKernel batch_kernel(uint32_t insert)
+{
+    if (insert == 1) return k_batch<1>;
+    if (insert == 2) return k_batch<2>;
+    return k_batch<0>;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host ---
+struct ising_batch {
+    std::vector<ising_lattice *> hs;
+    std::vector<uint64_t> sweeps;           // per lattice per run
+    uint32_t record_every = 0;
+    ising_batch_opts opts{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Allocator alloc;
+    // plan
+    std::vector<BatchStrip> strips;
+    std::vector<uint32_t> cta_first, cta_strips;
+    uint32_t grid = 0, block = 512, max_steps = 0;
+    size_t smem_bytes = 0;
+    std::vector<size_t> sample_base;        // first slot of each lattice in the counters
+    std::vector<size_t> nrec;               // sample slots of each lattice per run (the most a run can record)
+    size_t slots = 0;                       // recorded slots + one final slot per lattice
+    // device memory
+    void *d_plan = nullptr;                 // strips, cta_first, cta_strips, t0
+    size_t plan_bytes = 0;
+    void *d_work = nullptr;                 // borders, progress, counters, error flag
+    size_t work_bytes = 0;
+    size_t off_progress = 0, off_counters = 0, off_error = 0, off_t0 = 0;
+    size_t progress_bytes = 0;
+    unsigned long long *h_counters = nullptr;  // pinned
+    uint32_t *h_t0 = nullptr;                  // pinned
+    unsigned int *h_error = nullptr;           // pinned
+    cudaEvent_t ev = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    BatchLaunchArgs args{};
+    bool failed = false;
+};
+
+namespace {
+
+ising_status bfail(ising_batch *b, cudaError_t e, const char *what)
+{
+    if (b) {
+        b->failed = true;
+        for (ising_lattice *h : b->hs) h->failed = true;
+    }
+    return fail(ISING_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void free_batch(ising_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->alloc.release(b->d_plan, b->stream);
+    b->alloc.release(b->d_work, b->stream);
+    if (b->h_counters) cudaFreeHost(b->h_counters);
+    if (b->h_t0) cudaFreeHost(b->h_t0);
+    if (b->h_error) cudaFreeHost(b->h_error);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// Splits every lattice into strips and assigns them to CTAs (largest work
+// first, to the least loaded CTA with room in shared memory).
+ising_status make_plan(ising_batch *b)
+{
+    int dev = b->device;
+    int sms = 0, smem_optin = 0, smem_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (sms <= 0) return fail(ISING_ERR_CUDA, "no multiprocessors");
+    b->block = b->opts.block ? b->opts.block : 512;
+    const uint32_t ctas_per_sm = b->opts.ctas_per_sm ? b->opts.ctas_per_sm : 2;
+    // dynamic shared memory per CTA: the SM's share, less the kernel's static
+    // tables and the 1 KiB the runtime reserves per block
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, (const void *)batch_kernel(b->opts.insert));
+    const size_t reserve = fa.sharedSizeBytes + 1024;
+    size_t smem_cta = (size_t)smem_sm / ctas_per_sm;
+    smem_cta = smem_cta > reserve ? smem_cta - reserve : 0;
+    smem_cta = std::min<size_t>(smem_cta, (size_t)smem_optin > fa.sharedSizeBytes
+                                              ? (size_t)smem_optin - fa.sharedSizeBytes
+                                              : 0);
+    const uint32_t P = (uint32_t)sms * ctas_per_sm;
+
+    const size_t n = b->hs.size();
+    double total = 0;
+    for (size_t i = 0; i < n; ++i) total += (double)b->hs[i]->L * b->hs[i]->L * b->sweeps[i];
+    const double target = total / P;
+
+    struct S {
+        uint32_t lat, row0, nrows;
+        double work;
+        size_t bytes;
+    };
+    std::vector<S> parts;
+    std::vector<uint32_t> first_part(n), nparts(n);
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t L = b->hs[i]->L;
+        const size_t row_bytes = L / 8;
+        const double work = (double)L * L * b->sweeps[i];
+        uint64_t G = (uint64_t)std::max(1.0, std::round(work / std::max(target, 1.0)));
+        // a strip must fit in shared memory with its two halo rows
+        const uint64_t max_rows = smem_cta / row_bytes > 2 ? smem_cta / row_bytes - 2 : 0;
+        if (max_rows == 0) return fail(ISING_ERR_INVALID, "L = %llu rows do not fit in shared memory",
+                                       (unsigned long long)L);
+        // a strip's step must outweigh the cost of a border exchange: at least
+        // 2^17 sites per strip unless shared memory forces a finer split
+        G = std::min<uint64_t>(G, std::max<uint64_t>(1, L * L / (1ull << 17)));
+        G = std::max<uint64_t>(G, (L + max_rows - 1) / max_rows);
+        G = std::min<uint64_t>(G, L / 2);
+        first_part[i] = (uint32_t)parts.size();
+        nparts[i] = (uint32_t)G;
+        for (uint64_t k = 0; k < G; ++k) {
+            const uint64_t r0 = L * k / G, r1 = L * (k + 1) / G;
+            parts.push_back(S{(uint32_t)i, (uint32_t)r0, (uint32_t)(r1 - r0),
+                              work * (double)(r1 - r0) / (double)L, (r1 - r0 + 2) * row_bytes});
+        }
+    }
+    // largest first onto the least-loaded CTA with room
+    std::vector<uint32_t> order(parts.size());
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return parts[x].work > parts[y].work; });
+    std::vector<double> load(P, 0.0);
+    std::vector<size_t> used(P, 0);
+    std::vector<std::vector<uint32_t>> assigned(P);
+    std::vector<uint32_t> owner(parts.size());
+    for (uint32_t pi : order) {
+        int best = -1;
+        for (uint32_t c = 0; c < P; ++c) {
+            if (used[c] + parts[pi].bytes > smem_cta) continue;
+            if (assigned[c].size() >= kMaxStripsPerCta) continue;
+            if (best < 0 || load[c] < load[best]) best = (int)c;
+        }
+        if (best < 0)
+            return fail(ISING_ERR_INVALID,
+                        "the batch needs more shared memory than the GPU has (%zu bytes per CTA, %u CTAs)",
+                        smem_cta, P);
+        load[best] += parts[pi].work;
+        used[best] += parts[pi].bytes;
+        assigned[best].push_back(pi);
+        owner[pi] = (uint32_t)best;
+    }
+    // keep only CTAs with work; strips of a CTA in lattice/row order
+    b->strips.assign(parts.size(), BatchStrip{});
+    b->cta_first.clear();
+    b->cta_strips.clear();
+    size_t smem_max = 0;
+    for (uint32_t c = 0; c < P; ++c) {
+        if (assigned[c].empty()) continue;
+        std::sort(assigned[c].begin(), assigned[c].end());
+        b->cta_first.push_back((uint32_t)b->cta_strips.size());
+        size_t off_words = 0;
+        for (uint32_t pi : assigned[c]) {
+            b->cta_strips.push_back(pi);
+            b->strips[pi].smem_off = (uint32_t)off_words;
+            off_words += parts[pi].bytes / 8;
+        }
+        smem_max = std::max(smem_max, off_words * 8);
+    }
+    b->cta_first.push_back((uint32_t)b->cta_strips.size());
+    b->grid = (uint32_t)(b->cta_first.size() - 1);
+    b->smem_bytes = smem_max;
+
+    // strip descriptors (device pointers filled in after allocation)
+    b->max_steps = 0;
+    b->nrec.assign(n, 0);
+    b->sample_base.assign(n, 0);
+    size_t slot = 0;
+    for (size_t i = 0; i < n; ++i) {
+        ising_lattice *h = b->hs[i];
+        const uint64_t t0 = h->sweeps_done, ns = b->sweeps[i];
+        (void)t0;
+        // at most ceil(ns / record_every) samples in any run of ns sweeps
+        b->nrec[i] = b->record_every ? (ns + b->record_every - 1) / b->record_every : 0;
+        b->sample_base[i] = slot;
+        slot += b->nrec[i] + 1;  // + the final slot
+        b->max_steps = std::max<uint32_t>(b->max_steps, (uint32_t)(2 * ns));
+    }
+    b->slots = slot;
+    for (size_t pi = 0; pi < parts.size(); ++pi) {
+        const S &q = parts[pi];
+        ising_lattice *h = b->hs[q.lat];
+        BatchStrip &st = b->strips[pi];
+        st.L = h->L;
+        st.W = (uint32_t)(h->L / 64);
+        st.row0 = q.row0;
+        st.nrows = q.nrows;
+        const uint32_t k = (uint32_t)(pi - first_part[q.lat]), G = nparts[q.lat];
+        st.up_strip = first_part[q.lat] + (k + G - 1) % G;
+        st.dn_strip = first_part[q.lat] + (k + 1) % G;
+        st.nstrips_lat = G;
+        st.lat_index = q.lat;
+        st.nsteps = (uint32_t)(2 * b->sweeps[q.lat]);
+        st.record_every = b->record_every;
+        st.thr4 = h->thr4;
+        st.thr8 = h->thr8;
+        st.c3base = h->stream_id << 1;
+        st.key = h->key;
+    }
+    (void)owner;
+    return ISING_OK;
+}
+
+ising_status alloc_batch(ising_batch *b)
+{
+    const size_t n = b->hs.size();
+    const size_t ns = b->strips.size();
+    // plan block: strips | cta_first | cta_strips | t0
+    size_t off = 0;
+    const size_t off_strips = off;
+    off += ns * sizeof(BatchStrip);
+    off = (off + 15) & ~(size_t)15;
+    const size_t off_first = off;
+    off += b->cta_first.size() * 4;
+    off = (off + 15) & ~(size_t)15;
+    const size_t off_cstr = off;
+    off += b->cta_strips.size() * 4;
+    off = (off + 15) & ~(size_t)15;
+    b->off_t0 = off;
+    off += n * 4;
+    b->plan_bytes = (off + 255) & ~(size_t)255;
+    // work block: borders | progress | counters | error
+    size_t w = 0;
+    std::vector<size_t> border_off(ns, 0);
+    for (size_t i = 0; i < ns; ++i) {
+        if (b->strips[i].nstrips_lat > 1) {
+            border_off[i] = w;
+            w += 4ull * b->strips[i].W * 8;
+        }
+    }
+    w = (w + 255) & ~(size_t)255;
+    b->off_progress = w;
+    b->progress_bytes = ns * 4;
+    w += b->progress_bytes;
+    w = (w + 255) & ~(size_t)255;
+    b->off_counters = w;
+    w += b->slots * 16;
+    w = (w + 255) & ~(size_t)255;
+    b->off_error = w;
+    w += 256;
+    b->work_bytes = w;
+
+    b->d_plan = b->alloc.allocate(b->plan_bytes, b->stream);
+    b->d_work = b->alloc.allocate(b->work_bytes, b->stream);
+    if (!b->d_plan || !b->d_work) return fail(ISING_ERR_OOM, "cannot allocate the batch plan");
+    if (cudaHostAlloc((void **)&b->h_counters, b->slots * 16, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&b->h_t0, std::max<size_t>(n, 1) * 4, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&b->h_error, 16, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ISING_ERR_OOM, "cannot allocate pinned host memory for the batch");
+    }
+    char *work = static_cast<char *>(b->d_work);
+    for (size_t i = 0; i < ns; ++i) {
+        BatchStrip &st = b->strips[i];
+        ising_lattice *h = b->hs[st.lat_index];
+        st.lat = static_cast<uint64_t *>(h->d_spins);
+        st.border = st.nstrips_lat > 1 ? reinterpret_cast<uint64_t *>(work + border_off[i]) : nullptr;
+        st.progress = reinterpret_cast<unsigned int *>(work + b->off_progress) + i;
+        st.samples = reinterpret_cast<unsigned long long *>(work + b->off_counters) +
+                     2 * b->sample_base[st.lat_index];
+        st.final_counts = st.samples + 2 * b->nrec[st.lat_index];
+    }
+    std::vector<char> host(b->plan_bytes, 0);
+    std::memcpy(host.data() + off_strips, b->strips.data(), ns * sizeof(BatchStrip));
+    std::memcpy(host.data() + off_first, b->cta_first.data(), b->cta_first.size() * 4);
+    std::memcpy(host.data() + off_cstr, b->cta_strips.data(), b->cta_strips.size() * 4);
+    cudaError_t e = cudaMemcpyAsync(b->d_plan, host.data(), b->plan_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, e, "batch plan upload");
+
+    char *plan = static_cast<char *>(b->d_plan);
+    b->args.strips = reinterpret_cast<const BatchStrip *>(plan + off_strips);
+    b->args.cta_first = reinterpret_cast<const uint32_t *>(plan + off_first);
+    b->args.cta_strips = reinterpret_cast<const uint32_t *>(plan + off_cstr);
+    b->args.t0 = reinterpret_cast<const uint32_t *>(plan + b->off_t0);
+    b->args.max_steps = b->max_steps;
+    b->args.rows_per_item = b->opts.rows_per_item ? b->opts.rows_per_item : 4;
+    b->args.error_flag = reinterpret_cast<unsigned int *>(work + b->off_error);
+    const double ms = b->opts.wait_ms > 0 ? b->opts.wait_ms : 2000.0;
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->device);
+    b->args.wait_cycles = (long long)(ms * (clk_khz > 0 ? clk_khz : 2000000));
+    b->args.hold_strip = b->opts.hold_strip;
+    e = cudaFuncSetAttribute(batch_kernel(b->opts.insert), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)b->smem_bytes);
+    if (e != cudaSuccess) return bfail(b, e, "batch shared memory");
+    // every CTA must be resident at once
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->opts.insert), (int)b->block,
+                                                      b->smem_bytes);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return bfail(b, e, "batch occupancy");
+    if ((uint64_t)per_sm * (uint64_t)sms < b->grid)
+        return fail(ISING_ERR_INVALID, "batch plan needs %u resident CTAs, the GPU holds %d",
+                    b->grid, per_sm * sms);
+    return ISING_OK;
+}
+
+// Work of one run on the batch stream: clear the counters, progress and error
+// flag, copy the lattices' first sweep indices, launch, copy the counters and
+// the error flag back.
+cudaError_t enqueue_run(ising_batch *b)
+{
+    char *work = static_cast<char *>(b->d_work);
+    cudaError_t e = cudaMemsetAsync(work + b->off_progress, 0, b->work_bytes - b->off_progress, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char *>(b->d_plan) + b->off_t0, b->h_t0, b->hs.size() * 4,
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return e;
+    void *params[] = {&b->args};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(b->block);
+    cfg.dynamicSmemBytes = b->smem_bytes;
+    cfg.stream = b->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, (const void *)batch_kernel(b->opts.insert), params);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_counters, work + b->off_counters, b->slots * 16, cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_error, work + b->off_error, 4, cudaMemcpyDeviceToHost, b->stream);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
+                                          uint32_t record_every, const ising_batch_opts *opts,
+                                          ising_batch **out)
+{
+    clear_error();
+    if (!out) return fail(ISING_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!hs || !nsweeps || n == 0) return fail(ISING_ERR_INVALID, "empty batch");
+    for (uint32_t i = 0; i < n; ++i) {
+        ising_status st = check_live(hs[i]);
+        if (st != ISING_OK) return st;
+        if (hs[i]->device != hs[0]->device) return fail(ISING_ERR_INVALID, "handles on different devices");
+        if (nsweeps[i] == 0 || nsweeps[i] > (1u << 30))
+            return fail(ISING_ERR_INVALID, "sweeps per run must be in [1, 2^30]");
+        for (uint32_t k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return fail(ISING_ERR_INVALID, "a handle appears twice");
+    }
+    ising_batch *b = new (std::nothrow) ising_batch();
+    if (!b) return fail(ISING_ERR_OOM, "host allocation failed");
+    b->hs.assign(hs, hs + n);
+    b->sweeps.assign(nsweeps, nsweeps + n);
+    b->record_every = record_every;
+    if (opts) b->opts = *opts;
+    b->device = hs[0]->device;
+    b->alloc = current_allocator();
+    // a stream of the batch's own (the legacy default stream cannot be captured)
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(ISING_ERR_CUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+    if (b->opts.block != 0 && b->opts.block != 256 && b->opts.block != 512) {
+        delete b;
+        return fail(ISING_ERR_INVALID, "block must be 256 or 512");
+    }
+    if (b->opts.insert > 2 || b->opts.rows_per_item > 64) {
+        delete b;
+        return fail(ISING_ERR_INVALID, "bad batch options");
+    }
+    auto bail = [&](ising_status s) {
+        std::string msg = ising_last_error();
+        b->hs.clear();  // do not fail the handles for a planning error
+        free_batch(b);
+        fail(s, "%s", msg.c_str());
+        return s;
+    };
+    ising_status st;
+    for (ising_lattice *h : b->hs)
+        if ((st = harvest(h)) != ISING_OK) return bail(st);
+    if ((st = make_plan(b)) != ISING_OK) return bail(st);
+    if ((st = alloc_batch(b)) != ISING_OK) return bail(st);
+    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ISING_ERR_CUDA, "event creation failed"));
+    }
+    *out = b;
+    return ISING_OK;
+}
+
+ISING_API ising_status ising_batch_run(ising_batch *b, uint32_t runs)
+{
+    clear_error();
+    if (!b) return fail(ISING_ERR_INVALID, "null batch");
+    if (b->failed) return fail(ISING_ERR_STATE, "batch failed earlier");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail(b, e, "cudaSetDevice");
+    const size_t n = b->hs.size();
+    for (uint32_t r = 0; r < runs; ++r) {
+        for (size_t i = 0; i < n; ++i) {
+            ising_lattice *h = b->hs[i];
+            ising_status st = check_live(h);
+            if (st != ISING_OK) return st;
+            if ((st = harvest(h)) != ISING_OK) return st;
+            if (h->sweeps_done + b->sweeps[i] >= 0xFFFFFFFFull)
+                return fail(ISING_ERR_INVALID, "sweep counter would reach 2^32 - 1");
+            b->h_t0[i] = (uint32_t)h->sweeps_done;
+            // the lattice's own stream must be done with it first
+            if (h->stream != b->stream) {
+                if ((e = cudaEventRecord(h->ev, h->stream)) != cudaSuccess) return bfail(b, e, "event");
+                if ((e = cudaStreamWaitEvent(b->stream, h->ev, 0)) != cudaSuccess) return bfail(b, e, "wait");
+            }
+        }
+        if (b->opts.use_graph) {
+            if (!b->graph_exec) {
+                e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e2 = enqueue_run(b);
+                    e = cudaStreamEndCapture(b->stream, &b->graph);
+                    if (e2 != cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph_exec, b->graph, 0);
+                if (e != cudaSuccess) return bfail(b, e, "batch graph capture");
+            }
+            e = cudaGraphLaunch(b->graph_exec, b->stream);
+        } else {
+            e = enqueue_run(b);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b->ev);
+        if (e != cudaSuccess) return bfail(b, e, "batch run");
+        if (*b->h_error != 0u) {
+            b->failed = true;
+            for (ising_lattice *h : b->hs) h->failed = true;
+            return fail(ISING_ERR_TIMEOUT, "a strip waited longer than the limit; the lattices are lost");
+        }
+        for (size_t i = 0; i < n; ++i) {
+            ising_lattice *h = b->hs[i];
+            const unsigned long long *c = b->h_counters + 2 * b->sample_base[i];
+            const uint64_t t0 = h->sweeps_done;
+            const size_t got = b->record_every
+                                   ? (size_t)((t0 + b->sweeps[i]) / b->record_every - t0 / b->record_every)
+                                   : 0;
+            for (size_t k = 0; k < got; ++k) {
+                h->sM.push_back(to_M(h, c[2 * k]));
+                h->sE.push_back(to_E(h, c[2 * k + 1]));
+            }
+            h->M = to_M(h, c[2 * b->nrec[i]]);
+            h->E = to_E(h, c[2 * b->nrec[i] + 1]);
+            h->sweeps_done += b->sweeps[i];
+        }
+    }
+    return ISING_OK;
+}
+
+ISING_API ising_status ising_batch_info(const ising_batch *b, uint32_t *grid, uint32_t *block,
+                                        uint32_t *strips, size_t *smem_bytes)
+{
+    clear_error();
+    if (!b) return fail(ISING_ERR_INVALID, "null batch");
+    if (grid) *grid = b->grid;
+    if (block) *block = b->block;
+    if (strips) *strips = (uint32_t)b->strips.size();
+    if (smem_bytes) *smem_bytes = b->smem_bytes;
+    return ISING_OK;
+}
+
+ISING_API ising_status ising_batch_destroy(ising_batch *b)
+{
+    clear_error();
+    free_batch(b);
+    return ISING_OK;
+}
+
+ISING_API ising_status ising_sweep_batch(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
+                                         uint32_t record_every)
+{
+    ising_batch *b = nullptr;
+    ising_status st = ising_batch_create(hs, n, nsweeps, record_every, nullptr, &b);
+    if (st != ISING_OK) return st;
+    st = ising_batch_run(b, 1);
+    std::string msg = ising_last_error();
+    free_batch(b);
+    if (st != ISING_OK) fail(st, "%s", msg.c_str());
+    return st;
+}
+
+}  // extern "C"

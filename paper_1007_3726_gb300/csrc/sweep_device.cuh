@@ -1,0 +1,195 @@
+// Device building blocks of the checkerboard half-sweep shared by the
+// one-lattice kernel (kernels.cu) and the persistent multi-lattice kernel
+// (batch.cu): Philox4x32-10 rounds, the per-word acceptance masks and the
+// bit-sliced update of one word (Sec. 4, Eqs. 4-5).
+#pragma once
+
+#include "kernels.h"
+
+#include <cstdint>
+
+namespace ising {
+namespace {
+
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kWeylA = 0x9E3779B9u;
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+// Philox4x32 rounds r0 .. 9 in place (SC'11): the two multipliers act on
+// words 0 and 2; the new word 0 is hi(B * x2) ^ x1 ^ k0, word 1 is lo(B * x2),
+// word 2 is hi(A * x0) ^ x3 ^ k1, word 3 is lo(A * x0).
+template <int R0>
+__device__ __forceinline__ void philox_rounds_from(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                                   uint32_t &x3, const RoundKeys &k)
+{
+#pragma unroll
+    for (int r = R0; r < 10; ++r) {
+        const uint64_t pa = (uint64_t)x0 * kPhiloxMulA;
+        const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
+        const uint32_t n0 = (uint32_t)(pb >> 32) ^ x1 ^ k.k0[r];
+        const uint32_t n2 = (uint32_t)(pa >> 32) ^ x3 ^ k.k1[r];
+        x1 = (uint32_t)pb;
+        x3 = (uint32_t)pa;
+        x0 = n0;
+        x2 = n2;
+    }
+}
+
+__device__ __forceinline__ void philox_rounds(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                              uint32_t &x3, const RoundKeys &k)
+{
+    philox_rounds_from<0>(x0, x1, x2, x3, k);
+}
+
+template <typename Word>
+struct WordTraits;
+template <>
+struct WordTraits<uint32_t> {
+    static constexpr int bits = 32;
+    static constexpr uint32_t even = 0x55555555u;
+    __device__ static int popc(uint32_t v) { return __popc(v); }
+    __device__ static uint32_t from_halves(const uint32_t *h) { return h[0]; }
+};
+template <>
+struct WordTraits<uint64_t> {
+    static constexpr int bits = 64;
+    static constexpr uint64_t even = 0x5555555555555555ull;
+    __device__ static int popc(uint64_t v) { return __popcll(v); }
+    __device__ static uint64_t from_halves(const uint32_t *h)
+    {
+        return (uint64_t)h[0] | ((uint64_t)h[1] << 32);
+    }
+};
+
+// Block-wide sum of two per-thread counters, one 64-bit atomic each per block.
+__device__ __forceinline__ void block_accumulate(unsigned int a, unsigned int b,
+                                                 unsigned long long *acc)
+{
+    __shared__ unsigned long long red[2][32];
+    a = __reduce_add_sync(0xFFFFFFFFu, a);
+    b = __reduce_add_sync(0xFFFFFFFFu, b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = a;
+        red[1][warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        unsigned long long sa = lane < nw ? red[0][lane] : 0ull;
+        unsigned long long sb = lane < nw ? red[1][lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_down_sync(0xFFFFFFFFu, sa, o);
+            sb += __shfl_down_sync(0xFFFFFFFFu, sb, o);
+        }
+        if (lane == 0) {
+            atomicAdd(acc, sa);
+            atomicAdd(acc + 1, sb);
+        }
+    }
+}
+
+// The acceptance masks of one word whose first Philox group is g0: bit
+// 8q + 2l of half (q / 4) is set when draw l of the word's call q is below the
+// threshold.  Round 1 and the word-0/word-3 half of round 2 come from the
+// step-uniform values; the round-1 products A * (g0 + q) are one widening
+// multiply per word plus 64-bit additions of the constants A * q (the low
+// counter words g0 .. g0 + NB - 1 of a word never wrap, since g0 is a
+// multiple of NB).
+template <int NB, int INS>
+__device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t g0,
+                                                uint32_t (&p4)[(NB + 3) / 4],
+                                                uint32_t (&p8)[(NB + 3) / 4])
+{
+    const uint32_t c1 = (uint32_t)(g0 >> 32);  // the same for all groups of a word
+    uint32_t r2x2k = a.r2x2k, r2x3 = a.r2x3;
+    if (c1 != 0u) {
+        const uint64_t pa = (uint64_t)(a.r1x0 ^ c1) * kPhiloxMulA;
+        r2x2k = (uint32_t)(pa >> 32) ^ a.key.k1[1];
+        r2x3 = (uint32_t)pa;
+    }
+    const uint64_t pa0 = (uint64_t)(uint32_t)g0 * kPhiloxMulA;
+    // INS >= 1 (>= 2) starts the P4 (P8) mask from a zero the compiler cannot
+    // see, so that its bit insertions stay ORs on the ALU pipe instead of
+    // becoming additions on the pipe that also carries the Philox multiplies.
+#pragma unroll
+    for (int h = 0; h < (NB + 3) / 4; ++h) {
+        p4[h] = INS >= 1 ? a.zero : 0u;
+        p8[h] = INS >= 2 ? a.zero : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        // round 1: words 0, 1 are uniform (r1x0 ^ c1, lo(B t))
+        const uint64_t pa = pa0 + (uint64_t)kPhiloxMulA * (uint64_t)q;
+        const uint32_t x2 = (uint32_t)(pa >> 32) ^ a.r1x2k;
+        const uint32_t x3 = (uint32_t)pa;
+        // round 2: the product A * word 0 is uniform per word
+        const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
+        uint32_t y0 = (uint32_t)(pb >> 32) ^ a.r2x0k;
+        uint32_t y1 = (uint32_t)pb;
+        uint32_t y2 = x3 ^ r2x2k;
+        uint32_t y3 = r2x3;
+        philox_rounds_from<2>(y0, y1, y2, y3, a.key);
+        const uint32_t u[4] = {y0, y1, y2, y3};
+        const int h = q >> 2;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const uint32_t bit = 1u << (8 * (q & 3) + 2 * l);
+            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+                : "+r"(p4[h])
+                : "r"(u[l]), "r"(a.thr4), "r"(bit));
+            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+                : "+r"(p8[h])
+                : "r"(u[l]), "r"(a.thr8), "r"(bit));
+        }
+    }
+}
+
+// Update of one word of target sites (Sec. 4): cur is the word, up / dn the
+// words above / below, lw / rw the words left / right of it in its row, mask
+// the target bit positions, off their parity (0 or 1), g the Philox group of
+// the word's first byte.  Returns the new word; with count set, adds the
+// popcounts of the new word (+1 spins) and of the anti-aligned bonds of its
+// target sites.
+template <typename Word, int INS>
+__device__ __forceinline__ Word update_word(const HalfSweepArgs &a, Word cur, Word up, Word dn,
+                                            Word lw, Word rw, uint32_t off, uint64_t g, bool count,
+                                            unsigned int &cnt_up, unsigned int &cnt_anti)
+{
+    using Tr = WordTraits<Word>;
+    constexpr int B = Tr::bits;
+    constexpr int NB = B / 8;
+    const Word left = (cur << 1) | (lw >> (B - 1));   // bit b holds s(x - 1)
+    const Word right = (cur >> 1) | (rw << (B - 1));  // bit b holds s(x + 1)
+    const Word mask = off ? (Word)(Tr::even << 1) : Tr::even;
+
+    // energy variables and their bit-sliced sum c = i1 + i2 + i3 + i4
+    const Word i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
+    const Word s12 = i1 ^ i2, c12 = i1 & i2;
+    const Word s34 = i3 ^ i4, c34 = i3 & i4;
+    const Word odd = s12 ^ s34;                  // c odd
+    const Word ge2 = c12 | c34 | (s12 & s34);    // c >= 2: dE <= 0, always accepted
+    const Word eq1 = odd & ~ge2;                 // c == 1: dE = 4
+    const Word eq0 = ~(odd | ge2);               // c == 0: dE = 8
+
+    // the sites' draws: byte q of the word holds four target sites
+    uint32_t h4[(NB + 3) / 4], h8[(NB + 3) / 4];
+    word_draw_masks<NB, INS>(a, g, h4, h8);
+    const Word p4 = Tr::from_halves(h4) << off;
+    const Word p8 = Tr::from_halves(h8) << off;
+    const Word flip = mask & (ge2 | (eq1 & p4) | (eq0 & p8));
+    const Word nw = cur ^ flip;
+    if (count) {
+        // after the step: +1 spins of the word, and the anti-aligned bonds of
+        // its target sites (their neighbours are final)
+        cnt_up += Tr::popc(nw);
+        cnt_anti += Tr::popc(mask & (nw ^ up)) + Tr::popc(mask & (nw ^ dn)) +
+                    Tr::popc(mask & (nw ^ left)) + Tr::popc(mask & (nw ^ right));
+    }
+    return nw;
+}
+
+}  // namespace
+}  // namespace ising
