@@ -218,6 +218,78 @@ def run_reference(args, ws, rank):
 
 
 # -------------------------------------------------------------------- ours --
+def extras(P, stream):
+    """Other workloads, on rank 0 at N = 1: the L = 64 lattice (plain launches
+    against one persistent launch) and the 128-lattice finite-size-scaling batch
+    (one tuned persistent launch against sequential plain launches)."""
+    import numpy as np
+    import torch
+
+    from paper_1007_3726_gb300 import workloads as WL
+
+    out = {}
+    w = WL.plain_L64()
+    a = P.Lattice(**WL.lattice_kwargs(w))
+    a.sweep(20, 1)
+    a.measure()
+    t = time.perf_counter()
+    a.sweep(w["sweeps"], 1)
+    a.measure()
+    t_plain = time.perf_counter() - t
+    b_lat = P.Lattice(**WL.lattice_kwargs(w))
+    with P.Batch([b_lat], [w["sweeps"]], 1) as b:
+        b.run(1)
+        t = time.perf_counter()
+        b.run(1)
+        t_batch = time.perf_counter() - t
+    n64 = 64 * 64 * w["sweeps"]
+    out["L64_1000_sweeps"] = {"plain_attempts_per_ns": n64 / t_plain / 1e9,
+                              "persistent_attempts_per_ns": n64 / t_batch / 1e9,
+                              "note": "wall time of one call, M/E every sweep"}
+
+    specs = WL.fss_batch()
+    lats = [P.Lattice(**WL.lattice_kwargs(sp)) for sp in specs]
+    sweeps = [sp["sweeps"] for sp in specs]
+    N = sum(sp["L"] ** 2 for sp in specs)
+    opts, _ = P.ising_batch_tune(lats, sweeps, 20)
+    torch.cuda.synchronize()
+    with P.Batch(lats, sweeps, specs[0]["record_every"], **opts) as b:
+        info = b.info()
+        t = time.perf_counter()
+        b.run(1)
+        t_b = time.perf_counter() - t
+    # U4 per (L, T) with 20 % burn-in, and where the L=256 and L=512 curves cross
+    u4 = {}
+    nsamp = sweeps[0] // specs[0]["record_every"]
+    for sp, lat in zip(specs, lats):
+        d = lat.measure(first_sample=nsamp // 5)
+        u4.setdefault(sp["L"], []).append(d["U4"])
+    temps = WL.fss_temperatures()
+    cross = []
+    diff = np.array(u4[512]) - np.array(u4[256])
+    for i in range(len(temps) - 1):
+        if diff[i] > 0 >= diff[i + 1] or diff[i] < 0 <= diff[i + 1]:
+            cross.append(temps[i] + (temps[i + 1] - temps[i]) * diff[i] / (diff[i] - diff[i + 1]))
+    # sequential plain launches on the same lattices, 200 sweeps each
+    t = time.perf_counter()
+    for lat in lats:
+        lat.sweep(200, 10)
+    for lat in lats:
+        lat.measure()
+    t_p = time.perf_counter() - t
+    out["fss_batch_128_lattices"] = {
+        "persistent_attempts_per_ns": N * sweeps[0] / t_b / 1e9,
+        "sequential_plain_attempts_per_ns": N * 200 / t_p / 1e9,
+        "seconds": t_b, "plan": info, "options": opts,
+        "U4_crossings_L256_L512": cross,
+        "U4_burn_in": "first 20 % of the samples dropped",
+        "note": "10^4 sweeps of 128 lattices in one launch (wall time incl. sample read-back); "
+                "plain: 2 launches per sweep per lattice, 200 sweeps each"}
+    for lat in lats:
+        lat.close()
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
@@ -356,6 +428,8 @@ def run_ours(args, ws, rank, local):
         "observables_last_step": {"U4": obs["U4"], "mean_abs_m": obs["mean_abs_m"],
                                   "mean_e": obs["mean_e"], "n_samples": obs["n_samples"]},
     }
+    if ws == 1 and not args.no_extras:
+        line["extras"] = extras(P, stream)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -373,6 +447,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the L=64 and 128-lattice workloads")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

@@ -130,6 +130,11 @@ ISING_API ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t 
  */
 ISING_API ising_status ising_measure(ising_lattice *h, ising_obs *out);
 
+/* As ising_measure, but the moments use samples first_sample, first_sample+1,
+ * ... only (the equilibration samples before are dropped); n_samples counts
+ * the samples used. */
+ISING_API ising_status ising_measure_from(ising_lattice *h, uint64_t first_sample, ising_obs *out);
+
 /* Releases everything the handle owns.  NULL is a no-op; always returns ISING_OK
  * unless freeing reported a CUDA error. */
 ISING_API ising_status ising_destroy(ising_lattice *h);
@@ -248,6 +253,13 @@ ISING_API ising_status ising_batch_run(ising_batch *b, uint32_t runs);
 ISING_API ising_status ising_batch_info(const ising_batch *b, uint32_t *grid, uint32_t *block,
                                         uint32_t *strips, size_t *smem_bytes);
 ISING_API ising_status ising_batch_destroy(ising_batch *b);
+/* Times a few batch configurations (threads per CTA, CTAs per SM, rows per
+ * item) on probe runs of about probe_sweeps sweeps (0 = 20) and writes the
+ * fastest into *best (its other fields are kept from *best on entry); the
+ * lattices are saved before and restored after, the handles' counters and
+ * samples are untouched.  best_ms receives the probe run's time. */
+ISING_API ising_status ising_batch_tune(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
+                                        uint32_t probe_sweeps, ising_batch_opts *best, double *best_ms);
 /* One run of a batch made with default options, then destroyed. */
 ISING_API ising_status ising_sweep_batch(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
                                          uint32_t record_every);

@@ -20,10 +20,10 @@ from ._build import LIB_PATH, build  # noqa: F401
 
 __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
-    "ising_measure", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
+    "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
     "ising_device_spins", "ising_sweep_noalloc", "ising_get_launch", "ising_set_launch",
-    "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "Batch", "IsingBatchOpts",
+    "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "IsingBatchOpts",
     "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
 
@@ -98,6 +98,7 @@ def load(path: str | None = None):
         "ising_create": ([ctypes.POINTER(IsingParams), ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
         "ising_sweep": ([H, ctypes.c_uint64, ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64], ctypes.c_int),
         "ising_measure": ([H, ctypes.POINTER(IsingObs)], ctypes.c_int),
+        "ising_measure_from": ([H, ctypes.c_uint64, ctypes.POINTER(IsingObs)], ctypes.c_int),
         "ising_destroy": ([H], ctypes.c_int),
         "ising_get_spins": ([H, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
         "ising_get_packed": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
@@ -119,6 +120,8 @@ def load(path: str | None = None):
         "ising_batch_info": ([H, _u32p, _u32p, _u32p, _szp], ctypes.c_int),
         "ising_batch_destroy": ([H], ctypes.c_int),
         "ising_sweep_batch": ([ctypes.POINTER(H), ctypes.c_uint32, _u64p, ctypes.c_uint32], ctypes.c_int),
+        "ising_batch_tune": ([ctypes.POINTER(H), ctypes.c_uint32, _u64p, ctypes.c_uint32,
+                              ctypes.POINTER(IsingBatchOpts), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
@@ -174,6 +177,12 @@ def ising_sweep(h, nsweeps: int, record_every: int = 0, M_out=None, E_out=None, 
 def ising_measure(h) -> dict:
     o = IsingObs()
     _check(load().ising_measure(h, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def ising_measure_from(h, first_sample: int) -> dict:
+    o = IsingObs()
+    _check(load().ising_measure_from(h, first_sample, ctypes.byref(o)))
     return o.as_dict()
 
 
@@ -254,6 +263,16 @@ def ising_sweep_batch(lats, nsweeps, record_every: int = 0):
     arr = _handles(lats)
     ns = (ctypes.c_uint64 * len(lats))(*[int(x) for x in nsweeps])
     _check(load().ising_sweep_batch(arr, len(lats), ns, record_every))
+
+
+def ising_batch_tune(lats, nsweeps, probe_sweeps: int = 20, **base) -> tuple[dict, float]:
+    """Pick batch options by timing probe runs (the lattices are restored)."""
+    arr = _handles(lats)
+    ns = (ctypes.c_uint64 * len(lats))(*[int(x) for x in nsweeps])
+    o = IsingBatchOpts(**base)
+    ms = ctypes.c_double()
+    _check(load().ising_batch_tune(arr, len(lats), ns, probe_sweeps, ctypes.byref(o), ctypes.byref(ms)))
+    return {k: getattr(o, k) for k, _ in IsingBatchOpts._fields_}, ms.value
 
 
 class Batch:
@@ -372,8 +391,9 @@ class Lattice:
         ising_sweep(self._h, nsweeps, record_every, M, E, n)
         return M[:n], E[:n]
 
-    def measure(self) -> dict:
-        return ising_measure(self._h)
+    def measure(self, first_sample: int = 0) -> dict:
+        """Counters and FP64 moments of the samples from first_sample on."""
+        return ising_measure_from(self._h, first_sample) if first_sample else ising_measure(self._h)
 
     def spins(self, row0: int = 0, nrows: int | None = None) -> np.ndarray:
         nrows = self.L if nrows is None else nrows

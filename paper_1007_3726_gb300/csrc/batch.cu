@@ -45,6 +45,8 @@ struct BatchStrip {
     uint32_t nsteps;                    // 2 x sweeps of this launch
     uint32_t record_every;
     uint32_t thr4, thr8, c3base;        // thresholds, stream_id << 1
+    const unsigned int *up_progress, *dn_progress;  // the neighbouring strips' progress
+    const uint64_t *up_border, *dn_border;          // and border arrays
     RoundKeys key;
 };
 
@@ -55,6 +57,8 @@ struct BatchLaunchArgs {
     const uint32_t *t0;                 // first sweep index of each lattice in this launch
     uint32_t max_steps;
     uint32_t rows_per_item;
+    uint32_t max_strips;                // table entries per CTA
+    uint32_t table_words;               // 64-bit words of the tables before the strips' rows
     unsigned int *error_flag;           // set to 1 when a wait ran out
     long long wait_cycles;              // clock limit of one wait
     uint32_t hold_strip;                // 1 + index of a strip that never publishes (0 = none)
@@ -79,26 +83,24 @@ __device__ __forceinline__ void store_release(unsigned int *p, unsigned int v)
 // Thread 0 waits (bounded) until the neighbours of every multi-strip strip of
 // this CTA have completed `need` steps; the result is broadcast to the CTA.
 // Returns false when a wait ran out or another CTA reported a failure.
-__device__ bool wait_neighbours(const BatchLaunchArgs &A, uint32_t first, uint32_t last, uint32_t s)
+__device__ bool wait_neighbours(const BatchLaunchArgs &A, const BatchStrip *sst, uint32_t ns, uint32_t s)
 {
     __shared__ int ok;
     if (threadIdx.x == 0) {
         int good = 1;
         const long long start = clock64();
-        for (uint32_t j = first; j < last && good; ++j) {
-            const BatchStrip &st = A.strips[A.cta_strips[j]];
+        for (uint32_t k = 0; k < ns && good; ++k) {
+            const BatchStrip &st = sst[k];
             if (st.nstrips_lat == 1 || s >= st.nsteps) continue;
-            const unsigned int *pu = A.strips[st.up_strip].progress;
-            const unsigned int *pd = A.strips[st.dn_strip].progress;
-            unsigned int ns = 32;
-            while (!(load_acquire(pu) >= s && load_acquire(pd) >= s)) {
+            unsigned int ns_sleep = 32;
+            while (!(load_acquire(st.up_progress) >= s && load_acquire(st.dn_progress) >= s)) {
                 if (*(volatile unsigned int *)A.error_flag != 0u || clock64() - start > A.wait_cycles) {
                     atomicOr(A.error_flag, kFlagTimeout);
                     good = 0;
                     break;
                 }
-                __nanosleep(ns);
-                if (ns < 1024) ns <<= 1;
+                __nanosleep(ns_sleep);
+                if (ns_sleep < 1024) ns_sleep <<= 1;
             }
         }
         ok = good;
@@ -131,6 +133,52 @@ __device__ __forceinline__ void strip_step_args(HalfSweepArgs &a, const BatchStr
 
 constexpr uint32_t kMaxStripsPerCta = 64;
 
+// One item of a strip: R rows of one word column, or of one NQ-byte part of it
+// when 8 / NQ threads share the word (each writes only its own bytes).
+template <int INS, int NQ>
+__device__ __forceinline__ void batch_item(const BatchStrip &st, const HalfSweepArgs &a, uint32_t li,
+                                           uint32_t R, uint32_t p, bool count, unsigned int &cu,
+                                           unsigned int &ca)
+{
+    extern __shared__ uint64_t sm[];
+    constexpr uint32_t S = 8 / NQ;
+    const uint32_t W = st.W;
+    const uint32_t sub = (S == 1) ? 0u : (li & (S - 1));
+    const uint32_t rest = (S == 1) ? li : (li / S);  // S is a power of two: a shift
+    // words per row are a power of two for power-of-two L: a shift, else a division
+    const uint32_t rb = ((W & (W - 1)) == 0) ? (rest >> (31 - __clz(W))) : rest / W;
+    const uint32_t w = rest - rb * W;
+    const uint32_t wl = (w == 0) ? W - 1 : w - 1;
+    const uint32_t wr = (w + 1 == W) ? 0 : w + 1;
+    const uint32_t r0 = rb * R, r1 = min(r0 + R, st.nrows);
+    uint64_t *row = sm + st.smem_off + (uint64_t)(r0 + 1) * W;
+    uint64_t up = row[w - (uint64_t)W];
+    uint64_t cur = row[w];
+    const uint64_t groups_per_row = st.L >> 3;
+    const uint64_t y0 = (uint64_t)st.row0 + r0;
+    uint64_t g = y0 * groups_per_row + (uint64_t)w * 8u;
+    uint32_t off = (uint32_t)((y0 + p) & 1u);
+    for (uint32_t r = r0; r < r1; ++r) {
+        const uint64_t dn = row[W + w];
+        const uint64_t nw = update_word<uint64_t, INS, NQ>(a, cur, up, dn, row[wl], row[wr], off, g,
+                                                           count, cu, ca, sub * NQ);
+        if (NQ == 8) {
+            row[w] = nw;
+        } else if (NQ == 4) {
+            reinterpret_cast<uint32_t *>(row + w)[sub] = (uint32_t)(nw >> (32 * sub));
+        } else if (NQ == 2) {
+            reinterpret_cast<uint16_t *>(row + w)[sub] = (uint16_t)(nw >> (16 * sub));
+        } else {
+            reinterpret_cast<uint8_t *>(row + w)[sub] = (uint8_t)(nw >> (8 * sub));
+        }
+        up = nw;  // only bits of the other parity are read from it in the next row
+        cur = dn;
+        row += W;
+        g += groups_per_row;
+        off ^= 1u;
+    }
+}
+
 // Each step has four phases: wait for the neighbour strips of the previous
 // step, fill the halo rows of all strips, update all strips (one flat loop
 // over the (strip, row block, word) items of the CTA, so that small lattices
@@ -139,19 +187,32 @@ constexpr uint32_t kMaxStripsPerCta = 64;
 template <int INS>
 __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchLaunchArgs A)
 {
-    extern __shared__ uint64_t sm[];
-    __shared__ uint32_t item_end[kMaxStripsPerCta];   // prefix sums of the strips' items
-    __shared__ uint32_t strip_R[kMaxStripsPerCta];    // rows per item of each strip
-    __shared__ unsigned int cnt[kMaxStripsPerCta][2];  // step counters of each strip
-    __shared__ HalfSweepArgs sargs[kMaxStripsPerCta];  // step arguments of each strip
+    extern __shared__ uint64_t sm[];  // per-strip tables (A.table_words), then the strips' rows
+    __shared__ int cta_multi;         // does any strip exchange borders
+    const uint32_t MS = A.max_strips;
+    BatchStrip *sst = reinterpret_cast<BatchStrip *>(sm);                 // the CTA's strip descriptors
+    HalfSweepArgs *sargs = reinterpret_cast<HalfSweepArgs *>(sst + MS);   // their step arguments
+    uint32_t *item_end = reinterpret_cast<uint32_t *>(sargs + MS);       // prefix sums of their items
+    uint32_t *strip_R = item_end + MS;                                    // rows per item
+    uint32_t *strip_S = strip_R + MS;                                     // threads sharing one word
+    uint32_t *st0 = strip_S + MS;                                         // first sweep index
+    unsigned int (*cnt)[2] = reinterpret_cast<unsigned int (*)[2]>(st0 + MS);  // step counters
     __shared__ uint8_t scount[kMaxStripsPerCta];       // does the strip count in this step
     const uint32_t first = A.cta_first[blockIdx.x], last = A.cta_first[blockIdx.x + 1];
     const uint32_t ns = last - first;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) cta_multi = 0;
+    __syncthreads();
+    if (tid < ns) {
+        sst[tid] = A.strips[A.cta_strips[first + tid]];
+        st0[tid] = A.t0[sst[tid].lat_index];
+        if (sst[tid].nstrips_lat > 1) atomicOr(&cta_multi, 1);
+    }
+    __syncthreads();
 
     // the strips' rows into shared memory (row r of a strip at buffer row r + 1)
-    for (uint32_t j = first; j < last; ++j) {
-        const BatchStrip &st = A.strips[A.cta_strips[j]];
+    for (uint32_t j = 0; j < ns; ++j) {
+        const BatchStrip &st = sst[j];
         const uint64_t n = (uint64_t)st.nrows * st.W;
         const uint64_t *src = st.lat + (uint64_t)st.row0 * st.W;
         uint64_t *dst = sm + st.smem_off + st.W;
@@ -159,11 +220,14 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
     }
     if (tid == 0) {
         for (uint32_t k = 0; k < ns; ++k) {
-            const BatchStrip &st = A.strips[A.cta_strips[first + k]];
-            // enough items for every thread when the strip is small
-            uint32_t R = A.rows_per_item;
+            const BatchStrip &st = sst[k];
+            // enough items for every thread when the strip is small: fewer rows
+            // per item first, then fewer Philox calls per thread
+            uint32_t R = A.rows_per_item, S = 1;
             while (R > 1 && (uint64_t)((st.nrows + R - 1) / R) * st.W < nthr) R >>= 1;
+            while (S < 8 && (uint64_t)((st.nrows + R - 1) / R) * st.W * S < nthr) S <<= 1;
             strip_R[k] = R;
+            strip_S[k] = S;
         }
     }
     __syncthreads();
@@ -171,10 +235,10 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
     for (uint32_t s = 0; s < A.max_steps; ++s) {
         const uint32_t p = s & 1u;
         // 1. neighbours of the previous step
-        if (s > 0 && !wait_neighbours(A, first, last, s)) return;
+        if (s > 0 && cta_multi && !wait_neighbours(A, sst, ns, s)) return;
         // 2. halo rows, and the item ranges of this step
         for (uint32_t k = 0; k < ns; ++k) {
-            const BatchStrip &st = A.strips[A.cta_strips[first + k]];
+            const BatchStrip &st = sst[k];
             if (s >= st.nsteps) continue;
             const uint32_t W = st.W, nrows = st.nrows;
             uint64_t *buf = sm + st.smem_off;
@@ -192,8 +256,8 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
                 }
             } else {
                 const uint32_t pb = (s - 1) & 1u;
-                const uint64_t *bu = A.strips[st.up_strip].border + (uint64_t)(2 * pb + 1) * W;  // its bottom row
-                const uint64_t *bd = A.strips[st.dn_strip].border + (uint64_t)(2 * pb + 0) * W;  // its top row
+                const uint64_t *bu = st.up_border + (uint64_t)(2 * pb + 1) * W;  // its bottom row
+                const uint64_t *bd = st.dn_border + (uint64_t)(2 * pb + 0) * W;  // its top row
                 for (uint32_t i = tid; i < W; i += nthr) {
                     buf[i] = __ldcg(bu + i);
                     buf[(uint64_t)(nrows + 1) * W + i] = __ldcg(bd + i);
@@ -201,9 +265,9 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
             }
         }
         if (tid < ns) {
-            const BatchStrip &st = A.strips[A.cta_strips[first + tid]];
+            const BatchStrip &st = sst[tid];
             if (s < st.nsteps) {
-                const uint32_t t = A.t0[st.lat_index] + (s >> 1);
+                const uint32_t t = st0[tid] + (s >> 1);
                 HalfSweepArgs a;
                 strip_step_args(a, st, t, p);
                 sargs[tid] = a;
@@ -216,8 +280,8 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
         if (tid == 0) {
             uint32_t acc = 0;
             for (uint32_t k = 0; k < ns; ++k) {
-                const BatchStrip &st = A.strips[A.cta_strips[first + k]];
-                if (s < st.nsteps) acc += ((st.nrows + strip_R[k] - 1) / strip_R[k]) * st.W;
+                const BatchStrip &st = sst[k];
+                if (s < st.nsteps) acc += ((st.nrows + strip_R[k] - 1) / strip_R[k]) * st.W * strip_S[k];
                 item_end[k] = acc;
             }
         }
@@ -234,7 +298,7 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
                 kbase = item_end[k];
                 ++k;
             }
-            const BatchStrip &st = A.strips[A.cta_strips[first + k]];
+            const BatchStrip &st = sst[k];
             if (k != kc) {
                 if (count && (cu | ca)) {
                     atomicAdd(&cnt[kc][0], cu);
@@ -245,45 +309,41 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
                 count = scount[k] != 0;
             }
             const HalfSweepArgs &a = sargs[k];
-            const uint32_t W = st.W, R = strip_R[k];
             const uint32_t li = item - kbase;
-            const uint32_t rb = li / W, w = li - rb * W;
-            const uint32_t wl = (w == 0) ? W - 1 : w - 1;
-            const uint32_t wr = (w + 1 == W) ? 0 : w + 1;
-            const uint32_t r0 = rb * R, r1 = min(r0 + R, st.nrows);
-            uint64_t *row = sm + st.smem_off + (uint64_t)(r0 + 1) * W;
-            uint64_t up = row[w - (uint64_t)W];
-            uint64_t cur = row[w];
-            const uint64_t groups_per_row = st.L >> 3;
-            const uint64_t y0 = (uint64_t)st.row0 + r0;
-            uint64_t g = y0 * groups_per_row + (uint64_t)w * 8u;
-            uint32_t off = (uint32_t)((y0 + p) & 1u);
-            for (uint32_t r = r0; r < r1; ++r) {
-                const uint64_t dn = row[W + w];
-                const uint64_t nw = update_word<uint64_t, INS>(a, cur, up, dn, row[wl], row[wr], off, g,
-                                                               count, cu, ca);
-                row[w] = nw;
-                up = nw;
-                cur = dn;
-                row += W;
-                g += groups_per_row;
-                off ^= 1u;
+            switch (strip_S[k]) {
+            case 1: batch_item<INS, 8>(st, a, li, strip_R[k], p, count, cu, ca); break;
+            case 2: batch_item<INS, 4>(st, a, li, strip_R[k], p, count, cu, ca); break;
+            case 4: batch_item<INS, 2>(st, a, li, strip_R[k], p, count, cu, ca); break;
+            default: batch_item<INS, 1>(st, a, li, strip_R[k], p, count, cu, ca); break;
             }
         }
-        if (count && (cu | ca)) {
-            atomicAdd(&cnt[kc][0], cu);
-            atomicAdd(&cnt[kc][1], ca);
+        {
+            // warp-aggregated: one shared atomic per strip present in the warp
+            const uint32_t key = (count && (cu | ca)) ? kc : 0xFFFFFFFFu;
+            unsigned int rem = __ballot_sync(0xFFFFFFFFu, key != 0xFFFFFFFFu);
+            while (rem) {
+                const int leader = __ffs(rem) - 1;
+                const uint32_t kk = __shfl_sync(0xFFFFFFFFu, key, leader);
+                const bool mine = key == kk;
+                const unsigned int su = __reduce_add_sync(0xFFFFFFFFu, mine ? cu : 0u);
+                const unsigned int sa = __reduce_add_sync(0xFFFFFFFFu, mine ? ca : 0u);
+                if ((int)(tid & 31u) == leader) {
+                    atomicAdd(&cnt[kk][0], su);
+                    atomicAdd(&cnt[kk][1], sa);
+                }
+                rem &= ~__ballot_sync(0xFFFFFFFFu, mine);
+            }
         }
         __syncthreads();
 
         // 4. counters to the lattices' slots, boundary rows to the neighbours
         if (tid < ns) {
-            const BatchStrip &st = A.strips[A.cta_strips[first + tid]];
+            const BatchStrip &st = sst[tid];
             if (s < st.nsteps && p == 1u) {
-                const uint32_t t = A.t0[st.lat_index] + (s >> 1);
+                const uint32_t t = st0[tid] + (s >> 1);
                 const bool recorded = st.record_every != 0u && (t + 1) % st.record_every == 0u;
                 if (recorded) {
-                    const uint32_t slot = (t + 1) / st.record_every - A.t0[st.lat_index] / st.record_every - 1;
+                    const uint32_t slot = (t + 1) / st.record_every - st0[tid] / st.record_every - 1;
                     atomicAdd(st.samples + 2 * slot, (unsigned long long)cnt[tid][0]);
                     atomicAdd(st.samples + 2 * slot + 1, (unsigned long long)cnt[tid][1]);
                 }
@@ -295,8 +355,7 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
         }
         bool any_multi = false;
         for (uint32_t kk = 0; kk < ns; ++kk) {
-            const uint32_t si = A.cta_strips[first + kk];
-            const BatchStrip &st = A.strips[si];
+            const BatchStrip &st = sst[kk];
             if (st.nstrips_lat == 1 || s >= st.nsteps) continue;
             any_multi = true;
             const uint32_t W = st.W, nrows = st.nrows;
@@ -313,7 +372,7 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
             if (tid == 0) {
                 for (uint32_t kk = 0; kk < ns; ++kk) {
                     const uint32_t si = A.cta_strips[first + kk];
-                    const BatchStrip &st = A.strips[si];
+                    const BatchStrip &st = sst[kk];
                     if (st.nstrips_lat == 1 || s >= st.nsteps || A.hold_strip == si + 1) continue;
                     store_release(st.progress, s + 1);
                 }
@@ -323,8 +382,8 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
     }
 
     // the strips back to the lattices
-    for (uint32_t j = first; j < last; ++j) {
-        const BatchStrip &st = A.strips[A.cta_strips[j]];
+    for (uint32_t j = 0; j < ns; ++j) {
+        const BatchStrip &st = sst[j];
         const uint64_t n = (uint64_t)st.nrows * st.W;
         uint64_t *dst = st.lat + (uint64_t)st.row0 * st.W;
         const uint64_t *src = sm + st.smem_off + st.W;
@@ -359,7 +418,7 @@ struct ising_batch {
     // plan
     std::vector<BatchStrip> strips;
     std::vector<uint32_t> cta_first, cta_strips;
-    uint32_t grid = 0, block = 512, max_steps = 0;
+    uint32_t grid = 0, block = 512, max_steps = 0, max_strips = 0, table_words = 0;
     size_t smem_bytes = 0;
     std::vector<size_t> sample_base;        // first slot of each lattice in the counters
     std::vector<size_t> nrec;               // sample slots of each lattice per run (the most a run can record)
@@ -383,6 +442,10 @@ struct ising_batch {
 };
 
 namespace {
+
+// Bytes of the per-strip tables at the start of the kernel's shared memory.
+size_t table_entry_bytes() { return sizeof(BatchStrip) + sizeof(HalfSweepArgs) + 4 * 4 + 2 * 4; }
+size_t table_bytes(size_t max_strips) { return (max_strips * table_entry_bytes() + 15) & ~(size_t)15; }
 
 ising_status bfail(ising_batch *b, cudaError_t e, const char *what)
 {
@@ -421,7 +484,15 @@ ising_status make_plan(ising_batch *b)
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (sms <= 0) return fail(ISING_ERR_CUDA, "no multiprocessors");
     b->block = b->opts.block ? b->opts.block : 512;
-    const uint32_t ctas_per_sm = b->opts.ctas_per_sm ? b->opts.ctas_per_sm : 2;
+    uint32_t ctas_per_sm = b->opts.ctas_per_sm ? b->opts.ctas_per_sm : 2;
+    {
+        // no more CTAs per SM than the registers allow
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->opts.insert), (int)b->opts.block
+                                                              ? (int)b->opts.block : 512, 0) == cudaSuccess &&
+            occ > 0)
+            ctas_per_sm = std::min<uint32_t>(ctas_per_sm, (uint32_t)occ);
+    }
     // dynamic shared memory per CTA: the SM's share, less the kernel's static
     // tables and the 1 KiB the runtime reserves per block
     cudaFuncAttributes fa{};
@@ -446,67 +517,98 @@ ising_status make_plan(ising_batch *b)
     };
     std::vector<S> parts;
     std::vector<uint32_t> first_part(n), nparts(n);
-    for (size_t i = 0; i < n; ++i) {
-        const uint64_t L = b->hs[i]->L;
-        const size_t row_bytes = L / 8;
-        const double work = (double)L * L * b->sweeps[i];
-        uint64_t G = (uint64_t)std::max(1.0, std::round(work / std::max(target, 1.0)));
-        // a strip must fit in shared memory with its two halo rows
-        const uint64_t max_rows = smem_cta / row_bytes > 2 ? smem_cta / row_bytes - 2 : 0;
-        if (max_rows == 0) return fail(ISING_ERR_INVALID, "L = %llu rows do not fit in shared memory",
-                                       (unsigned long long)L);
-        // a strip's step must outweigh the cost of a border exchange: at least
-        // 2^17 sites per strip unless shared memory forces a finer split
-        G = std::min<uint64_t>(G, std::max<uint64_t>(1, L * L / (1ull << 17)));
-        G = std::max<uint64_t>(G, (L + max_rows - 1) / max_rows);
-        G = std::min<uint64_t>(G, L / 2);
-        first_part[i] = (uint32_t)parts.size();
-        nparts[i] = (uint32_t)G;
-        for (uint64_t k = 0; k < G; ++k) {
-            const uint64_t r0 = L * k / G, r1 = L * (k + 1) / G;
-            parts.push_back(S{(uint32_t)i, (uint32_t)r0, (uint32_t)(r1 - r0),
-                              work * (double)(r1 - r0) / (double)L, (r1 - r0 + 2) * row_bytes});
+    std::vector<std::vector<uint32_t>> assigned;
+    // Packing can fail on fragmentation although the total fits: retry with
+    // strips of at most half, a quarter, ... of a CTA's shared memory.
+    bool packed = false;
+    for (int attempt = 0; attempt < 6 && !packed; ++attempt) {
+        const size_t strip_cap = smem_cta >> attempt;
+        parts.clear();
+        bool fits = true;
+        for (size_t i = 0; i < n && fits; ++i) {
+            const uint64_t L = b->hs[i]->L;
+            const size_t row_bytes = L / 8;
+            const double work = (double)L * L * b->sweeps[i];
+            uint64_t G = (uint64_t)std::max(1.0, std::round(work / std::max(target, 1.0)));
+            // a strip must fit in shared memory with its two halo rows
+            const uint64_t max_rows = strip_cap / row_bytes > 2 ? strip_cap / row_bytes - 2 : 0;
+            if (max_rows == 0) {
+                fits = false;
+                break;
+            }
+            // a strip's step must outweigh the cost of a border exchange: at least
+            // 2^17 sites per strip unless shared memory forces a finer split
+            G = std::min<uint64_t>(G, std::max<uint64_t>(1, L * L / (1ull << 17)));
+            G = std::max<uint64_t>(G, (L + max_rows - 1) / max_rows);
+            G = std::min<uint64_t>(G, L / 2);
+            first_part[i] = (uint32_t)parts.size();
+            nparts[i] = (uint32_t)G;
+            for (uint64_t k = 0; k < G; ++k) {
+                const uint64_t r0 = L * k / G, r1 = L * (k + 1) / G;
+                parts.push_back(S{(uint32_t)i, (uint32_t)r0, (uint32_t)(r1 - r0),
+                                  work * (double)(r1 - r0) / (double)L,
+                                  (r1 - r0 + 2) * row_bytes + table_entry_bytes()});
+            }
+        }
+        if (!fits) break;
+        // largest first onto the least-loaded CTA with room
+        std::vector<uint32_t> order(parts.size());
+        std::iota(order.begin(), order.end(), 0u);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t x, uint32_t y) { return parts[x].work > parts[y].work; });
+        std::vector<double> load(P, 0.0);
+        std::vector<size_t> used(P, 0);
+        assigned.assign(P, {});
+        packed = true;
+        for (uint32_t pi : order) {
+            int best = -1;
+            for (uint32_t c = 0; c < P; ++c) {
+                if (used[c] + parts[pi].bytes > smem_cta) continue;
+                if (assigned[c].size() >= kMaxStripsPerCta) continue;
+                if (best < 0 || load[c] < load[best]) best = (int)c;
+            }
+            if (best < 0) {
+                packed = false;
+                break;
+            }
+            load[best] += parts[pi].work;
+            used[best] += parts[pi].bytes;
+            assigned[best].push_back(pi);
+        }
+        if (packed) {
+            // every CTA gets a table of the largest CTA's strip count
+            size_t ms = 0, rows_max = 0;
+            for (uint32_t c = 0; c < P; ++c) {
+                ms = std::max(ms, assigned[c].size());
+                size_t r = 0;
+                for (uint32_t pi : assigned[c]) r += parts[pi].bytes - table_entry_bytes();
+                rows_max = std::max(rows_max, r);
+            }
+            if (table_bytes(ms) + rows_max > smem_cta) packed = false;
         }
     }
-    // largest first onto the least-loaded CTA with room
-    std::vector<uint32_t> order(parts.size());
-    std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t x, uint32_t y) { return parts[x].work > parts[y].work; });
-    std::vector<double> load(P, 0.0);
-    std::vector<size_t> used(P, 0);
-    std::vector<std::vector<uint32_t>> assigned(P);
-    std::vector<uint32_t> owner(parts.size());
-    for (uint32_t pi : order) {
-        int best = -1;
-        for (uint32_t c = 0; c < P; ++c) {
-            if (used[c] + parts[pi].bytes > smem_cta) continue;
-            if (assigned[c].size() >= kMaxStripsPerCta) continue;
-            if (best < 0 || load[c] < load[best]) best = (int)c;
-        }
-        if (best < 0)
-            return fail(ISING_ERR_INVALID,
-                        "the batch needs more shared memory than the GPU has (%zu bytes per CTA, %u CTAs)",
-                        smem_cta, P);
-        load[best] += parts[pi].work;
-        used[best] += parts[pi].bytes;
-        assigned[best].push_back(pi);
-        owner[pi] = (uint32_t)best;
-    }
+    if (!packed)
+        return fail(ISING_ERR_INVALID,
+                    "the batch needs more shared memory than the GPU has (%zu bytes per CTA, %u CTAs)",
+                    smem_cta, P);
     // keep only CTAs with work; strips of a CTA in lattice/row order
     b->strips.assign(parts.size(), BatchStrip{});
     b->cta_first.clear();
     b->cta_strips.clear();
+    size_t max_strips = 0;
+    for (uint32_t c = 0; c < P; ++c) max_strips = std::max(max_strips, assigned[c].size());
+    b->max_strips = (uint32_t)max_strips;
+    b->table_words = (uint32_t)(table_bytes(max_strips) / 8);
     size_t smem_max = 0;
     for (uint32_t c = 0; c < P; ++c) {
         if (assigned[c].empty()) continue;
         std::sort(assigned[c].begin(), assigned[c].end());
         b->cta_first.push_back((uint32_t)b->cta_strips.size());
-        size_t off_words = 0;
+        size_t off_words = b->table_words;
         for (uint32_t pi : assigned[c]) {
             b->cta_strips.push_back(pi);
             b->strips[pi].smem_off = (uint32_t)off_words;
-            off_words += parts[pi].bytes / 8;
+            off_words += (parts[pi].bytes - table_entry_bytes()) / 8;
         }
         smem_max = std::max(smem_max, off_words * 8);
     }
@@ -550,7 +652,6 @@ ising_status make_plan(ising_batch *b)
         st.c3base = h->stream_id << 1;
         st.key = h->key;
     }
-    (void)owner;
     return ISING_OK;
 }
 
@@ -613,6 +714,13 @@ ising_status alloc_batch(ising_batch *b)
                      2 * b->sample_base[st.lat_index];
         st.final_counts = st.samples + 2 * b->nrec[st.lat_index];
     }
+    for (size_t i = 0; i < ns; ++i) {
+        BatchStrip &st = b->strips[i];
+        st.up_progress = b->strips[st.up_strip].progress;
+        st.dn_progress = b->strips[st.dn_strip].progress;
+        st.up_border = b->strips[st.up_strip].border;
+        st.dn_border = b->strips[st.dn_strip].border;
+    }
     std::vector<char> host(b->plan_bytes, 0);
     std::memcpy(host.data() + off_strips, b->strips.data(), ns * sizeof(BatchStrip));
     std::memcpy(host.data() + off_first, b->cta_first.data(), b->cta_first.size() * 4);
@@ -628,6 +736,8 @@ ising_status alloc_batch(ising_batch *b)
     b->args.t0 = reinterpret_cast<const uint32_t *>(plan + b->off_t0);
     b->args.max_steps = b->max_steps;
     b->args.rows_per_item = b->opts.rows_per_item ? b->opts.rows_per_item : 4;
+    b->args.max_strips = b->max_strips;
+    b->args.table_words = b->table_words;
     b->args.error_flag = reinterpret_cast<unsigned int *>(work + b->off_error);
     const double ms = b->opts.wait_ms > 0 ? b->opts.wait_ms : 2000.0;
     int clk_khz = 0;
@@ -826,6 +936,98 @@ ISING_API ising_status ising_batch_destroy(ising_batch *b)
 {
     clear_error();
     free_batch(b);
+    return ISING_OK;
+}
+
+ISING_API ising_status ising_batch_tune(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
+                                        uint32_t probe_sweeps, ising_batch_opts *best, double *best_ms)
+{
+    clear_error();
+    if (!best) return fail(ISING_ERR_INVALID, "best is NULL");
+    if (!hs || !nsweeps || n == 0) return fail(ISING_ERR_INVALID, "empty batch");
+    if (probe_sweeps == 0) probe_sweeps = 20;
+    for (uint32_t i = 0; i < n; ++i) {
+        ising_status st = check_live(hs[i]);
+        if (st != ISING_OK) return st;
+        if ((st = harvest(hs[i])) != ISING_OK) return st;
+    }
+    // the candidates are timed on the real lattices, which are saved first and
+    // restored afterwards; the handles' counters and samples are not touched
+    size_t total = 0;
+    for (uint32_t i = 0; i < n; ++i) total += hs[i]->bytes;
+    Allocator al = current_allocator();
+    cudaStream_t s0 = hs[0]->stream;
+    char *save = static_cast<char *>(al.allocate(total, s0));
+    if (!save) return fail(ISING_ERR_OOM, "cannot allocate %zu bytes to save the lattices", total);
+    cudaError_t e = cudaSuccess;
+    size_t off = 0;
+    for (uint32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaMemcpyAsync(save + off, hs[i]->d_spins, hs[i]->bytes, cudaMemcpyDeviceToDevice,
+                            hs[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(hs[i]->stream);
+        off += hs[i]->bytes;
+    }
+    // probe sweeps in proportion to the requested ones (at least one each)
+    uint64_t maxn = 1;
+    for (uint32_t i = 0; i < n; ++i) maxn = std::max<uint64_t>(maxn, nsweeps[i]);
+    std::vector<uint64_t> probe(n);
+    for (uint32_t i = 0; i < n; ++i)
+        probe[i] = std::max<uint64_t>(1, (uint64_t)((double)probe_sweeps * nsweeps[i] / maxn + 0.5));
+    struct Cand {
+        uint32_t block, ctas, rows;
+    };
+    const Cand cands[] = {{256, 4, 4}, {256, 4, 8}, {256, 3, 4}, {256, 2, 4},
+                          {512, 2, 4}, {512, 2, 8}, {512, 1, 4}, {256, 8, 4}};
+    double best_t = 1e300;
+    bool found = false;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    for (const Cand &c : cands) {
+        if (e != cudaSuccess) break;
+        ising_batch_opts o = *best;
+        o.block = c.block;
+        o.ctas_per_sm = c.ctas;
+        o.rows_per_item = c.rows;
+        o.use_graph = 0;
+        o.hold_strip = 0;
+        ising_batch *b = nullptr;
+        if (ising_batch_create(hs, n, probe.data(), 0, &o, &b) != ISING_OK) continue;  // plan does not fit
+        for (uint32_t i = 0; i < n; ++i) b->h_t0[i] = (uint32_t)hs[i]->sweeps_done;
+        float ms = 0;
+        e = enqueue_run(b);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+        if (e == cudaSuccess) e = enqueue_run(b);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        const bool ok = e == cudaSuccess && *b->h_error == 0u;
+        b->hs.clear();  // the handles are not part of the probe's failure
+        free_batch(b);
+        if (ok && ms < best_t) {
+            best_t = ms;
+            *best = o;
+            found = true;
+        }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    off = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        cudaError_t e2 = cudaMemcpyAsync(hs[i]->d_spins, save + off, hs[i]->bytes,
+                                         cudaMemcpyDeviceToDevice, hs[i]->stream);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(hs[i]->stream);
+        if (e == cudaSuccess) e = e2;
+        off += hs[i]->bytes;
+    }
+    al.release(save, s0);
+    if (e != cudaSuccess) {
+        for (uint32_t i = 0; i < n; ++i) hs[i]->failed = true;
+        return fail(ISING_ERR_CUDA, "batch tuning: %s", cudaGetErrorString(e));
+    }
+    if (!found) return fail(ISING_ERR_INVALID, "no batch configuration fits the lattices");
+    best->use_graph = 0;
+    if (best_ms) *best_ms = best_t;
     return ISING_OK;
 }
 

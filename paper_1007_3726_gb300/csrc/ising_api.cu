@@ -394,7 +394,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
     return ISING_OK;
 }
 
-ising_status ising_measure(ising_lattice *h, ising_obs *out)
+ising_status ising_measure_from(ising_lattice *h, uint64_t first_sample, ising_obs *out)
 {
     clear_error();
     ising_status st = check_live(h);
@@ -404,15 +404,15 @@ ising_status ising_measure(ising_lattice *h, ising_obs *out)
     CK(h, cudaStreamSynchronize(h->stream));
     std::memset(out, 0, sizeof *out);
     out->sweeps_done = h->sweeps_done;
-    out->n_samples = h->sM.size();
+    out->n_samples = h->sM.size() > first_sample ? h->sM.size() - first_sample : 0;
     out->M = h->M;
     out->E = h->E;
     const size_t n = h->sM.size();
-    if (n == 0) return ISING_OK;
+    if (out->n_samples == 0) return ISING_OK;
     // plain FP64 sums in sample order
     const double N = (double)h->L * (double)h->L;
     double sm = 0, sa = 0, s2 = 0, s4 = 0, se = 0, se2 = 0;
-    for (size_t i = 0; i < n; ++i) {
+    for (size_t i = (size_t)first_sample; i < n; ++i) {
         const double m = (double)h->sM[i] / N;
         const double e = (double)h->sE[i] / N;
         sm += m;
@@ -422,7 +422,7 @@ ising_status ising_measure(ising_lattice *h, ising_obs *out)
         se += e;
         se2 += e * e;
     }
-    const double k = (double)n;
+    const double k = (double)(n - first_sample);
     out->mean_m = sm / k;
     out->mean_abs_m = sa / k;
     out->mean_m2 = s2 / k;
@@ -434,6 +434,8 @@ ising_status ising_measure(ising_lattice *h, ising_obs *out)
     out->C = N * (out->mean_e2 - out->mean_e * out->mean_e) / (h->T * h->T);
     return ISING_OK;
 }
+
+ising_status ising_measure(ising_lattice *h, ising_obs *out) { return ising_measure_from(h, 0, out); }
 
 ising_status ising_get_spins(ising_lattice *h, uint64_t row0, uint64_t nrows, int8_t *out)
 {

@@ -98,10 +98,10 @@ __device__ __forceinline__ void block_accumulate(unsigned int a, unsigned int b,
 // multiply per word plus 64-bit additions of the constants A * q (the low
 // counter words g0 .. g0 + NB - 1 of a word never wrap, since g0 is a
 // multiple of NB).
-template <int NB, int INS>
+template <int NB, int INS, int NQ = NB>
 __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t g0,
                                                 uint32_t (&p4)[(NB + 3) / 4],
-                                                uint32_t (&p8)[(NB + 3) / 4])
+                                                uint32_t (&p8)[(NB + 3) / 4], uint32_t q0 = 0)
 {
     const uint32_t c1 = (uint32_t)(g0 >> 32);  // the same for all groups of a word
     uint32_t r2x2k = a.r2x2k, r2x3 = a.r2x3;
@@ -114,13 +114,18 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
     // INS >= 1 (>= 2) starts the P4 (P8) mask from a zero the compiler cannot
     // see, so that its bit insertions stay ORs on the ALU pipe instead of
     // becoming additions on the pipe that also carries the Philox multiplies.
+    // With NQ < NB the calls q0 .. q0 + NQ - 1 (within one 32-bit half, since q0
+    // is a multiple of NQ <= 4) are accumulated at their offsets from q0.
+    constexpr int NH = (NQ == NB) ? (NB + 3) / 4 : 1;
+    uint32_t m4[NH], m8[NH];
 #pragma unroll
-    for (int h = 0; h < (NB + 3) / 4; ++h) {
-        p4[h] = INS >= 1 ? a.zero : 0u;
-        p8[h] = INS >= 2 ? a.zero : 0u;
+    for (int h = 0; h < NH; ++h) {
+        m4[h] = INS >= 1 ? a.zero : 0u;
+        m8[h] = INS >= 2 ? a.zero : 0u;
     }
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
+    for (int qq = 0; qq < NQ; ++qq) {
+        const uint32_t q = (NQ == NB) ? (uint32_t)qq : q0 + (uint32_t)qq;
         // round 1: words 0, 1 are uniform (r1x0 ^ c1, lo(B t))
         const uint64_t pa = pa0 + (uint64_t)kPhiloxMulA * (uint64_t)q;
         const uint32_t x2 = (uint32_t)(pa >> 32) ^ a.r1x2k;
@@ -133,16 +138,31 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
         uint32_t y3 = r2x3;
         philox_rounds_from<2>(y0, y1, y2, y3, a.key);
         const uint32_t u[4] = {y0, y1, y2, y3};
-        const int h = q >> 2;
+        const int h = (NQ == NB) ? (qq >> 2) : 0;
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-            const uint32_t bit = 1u << (8 * (q & 3) + 2 * l);
+            const uint32_t bit = 1u << (8 * (qq & 3) + 2 * l);
             asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
-                : "+r"(p4[h])
+                : "+r"(m4[h])
                 : "r"(u[l]), "r"(a.thr4), "r"(bit));
             asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
-                : "+r"(p8[h])
+                : "+r"(m8[h])
                 : "r"(u[l]), "r"(a.thr8), "r"(bit));
+        }
+    }
+    if (NQ == NB) {
+#pragma unroll
+        for (int h = 0; h < (NB + 3) / 4; ++h) {
+            p4[h] = m4[(NQ == NB) ? h : 0];
+            p8[h] = m8[(NQ == NB) ? h : 0];
+        }
+    } else {
+        const uint32_t sh = 8u * (q0 & 3u);
+#pragma unroll
+        for (int h = 0; h < (NB + 3) / 4; ++h) {
+            const bool mine = (uint32_t)h == (q0 >> 2);
+            p4[h] = mine ? (m4[0] << sh) : 0u;
+            p8[h] = mine ? (m8[0] << sh) : 0u;
         }
     }
 }
@@ -153,10 +173,14 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
 // the word's first byte.  Returns the new word; with count set, adds the
 // popcounts of the new word (+1 spins) and of the anti-aligned bonds of its
 // target sites.
-template <typename Word, int INS>
+// With NQ < NB only the Philox calls (bytes) q0 .. q0 + NQ - 1 of the word are
+// drawn and only those bytes of the returned word (and of the counts) are
+// meaningful: several threads can then share one word.
+template <typename Word, int INS, int NQ = WordTraits<Word>::bits / 8>
 __device__ __forceinline__ Word update_word(const HalfSweepArgs &a, Word cur, Word up, Word dn,
                                             Word lw, Word rw, uint32_t off, uint64_t g, bool count,
-                                            unsigned int &cnt_up, unsigned int &cnt_anti)
+                                            unsigned int &cnt_up, unsigned int &cnt_anti,
+                                            uint32_t q0 = 0)
 {
     using Tr = WordTraits<Word>;
     constexpr int B = Tr::bits;
@@ -176,17 +200,20 @@ __device__ __forceinline__ Word update_word(const HalfSweepArgs &a, Word cur, Wo
 
     // the sites' draws: byte q of the word holds four target sites
     uint32_t h4[(NB + 3) / 4], h8[(NB + 3) / 4];
-    word_draw_masks<NB, INS>(a, g, h4, h8);
+    word_draw_masks<NB, INS, NQ>(a, g, h4, h8, q0);
     const Word p4 = Tr::from_halves(h4) << off;
     const Word p8 = Tr::from_halves(h8) << off;
-    const Word flip = mask & (ge2 | (eq1 & p4) | (eq0 & p8));
+    Word sel = mask;
+    if (NQ < NB) sel &= (((Word)1 << (8 * NQ)) - 1) << (8 * q0);  // this thread's bytes
+    const Word flip = sel & (ge2 | (eq1 & p4) | (eq0 & p8));
     const Word nw = cur ^ flip;
     if (count) {
         // after the step: +1 spins of the word, and the anti-aligned bonds of
         // its target sites (their neighbours are final)
-        cnt_up += Tr::popc(nw);
-        cnt_anti += Tr::popc(mask & (nw ^ up)) + Tr::popc(mask & (nw ^ dn)) +
-                    Tr::popc(mask & (nw ^ left)) + Tr::popc(mask & (nw ^ right));
+        const Word own = (NQ < NB) ? ((((Word)1 << (8 * NQ)) - 1) << (8 * q0)) : ~(Word)0;
+        cnt_up += Tr::popc(nw & own);
+        cnt_anti += Tr::popc(sel & (nw ^ up)) + Tr::popc(sel & (nw ^ dn)) +
+                    Tr::popc(sel & (nw ^ left)) + Tr::popc(sel & (nw ^ right));
     }
     return nw;
 }

@@ -170,3 +170,19 @@ def test_batch_rejects_bad_input(P):
         P.ising_sweep_batch([a], [0], 0)
     with pytest.raises(P.IsingError):
         P.Batch([a], [1], 0, block=1024)
+
+
+def test_batch_tune_restores_lattices_and_results_stay_exact(P):
+    specs = SPECS[:7]
+    sweeps = [5, 4, 3, 6, 2, 3, 4]
+    ref = _reference(P, specs, sweeps, 1)
+    lats = _make(P, specs)
+    before = [l.spins() for l in lats]
+    opts, ms = P.ising_batch_tune(lats, sweeps, 4)
+    assert ms > 0 and opts["block"] in (256, 512)
+    for l, s0 in zip(lats, before):
+        assert np.array_equal(l.spins(), s0)
+        assert l.measure()["sweeps_done"] == 0
+    with P.Batch(lats, sweeps, 1, **opts) as b:
+        b.run(1)
+    _check(P, lats, ref)

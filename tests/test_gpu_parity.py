@@ -80,6 +80,12 @@ def test_plain_method_L64_1000_sweeps(P, orc):
         assert d[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-300), k
     assert d["n_samples"] == 1000 and d["sweeps_done"] == 1000
     assert (d["M"], d["E"]) == (int(Mo[-1]), int(Eo[-1]))
+    # with the first 200 samples dropped as equilibration
+    d2 = lat.measure(first_sample=200)
+    ref2 = orc.moments(Mo, Eo, N=64 * 64, T=2.269185, burn=200)
+    assert d2["n_samples"] == 800
+    for k in ("mean_abs_m", "mean_m2", "mean_m4", "mean_e", "U4", "chi", "C"):
+        assert d2[k] == pytest.approx(ref2[k], rel=1e-12, abs=1e-300), k
 
 
 def test_split_calls_and_record_every_are_invariant(P, orc):
