@@ -76,6 +76,10 @@ def _load():
     lib.orc_run_window.argtypes = [_i8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                    ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+    lib.orc_cold_tiled_counts.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_uint32, _i64p, _i64p]
+    lib.orc_cold_tiled_counts.restype = ctypes.c_int
     lib.orc_moments.argtypes = [_i64p, _i64p, ctypes.c_uint64, ctypes.c_uint64,
                                 ctypes.c_double, ctypes.c_double, _dblp]
     lib.orc_moments.restype = ctypes.c_uint64
@@ -181,6 +185,19 @@ def run_window(s: np.ndarray, L: int, row0: int, nsweeps: int, seed: int, stream
     assert s.dtype == np.int8 and s.flags.c_contiguous and s.shape[1] == L
     _load().orc_run_window(_ptr(s, ctypes.c_int8), L, row0, s.shape[0], t0, nsweeps, seed,
                            stream_id, thr4, thr8)
+
+
+def cold_tiled_counts(L: int, k: int, seed: int, stream_id: int, thr4: int, thr8: int,
+                      up: bool = True, tile_rows: int = 1024):
+    """M, E of the whole L x L lattice after each of its first k sweeps from a cold
+    start, tile by tile in light-cone windows (no L x L array is held)."""
+    M = np.zeros(k, dtype=np.int64)
+    E = np.zeros(k, dtype=np.int64)
+    rc = _load().orc_cold_tiled_counts(L, 1 if up else 0, k, tile_rows, seed, stream_id, thr4, thr8,
+                                       _ptr(M, ctypes.c_int64), _ptr(E, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("tile_rows must divide L and leave room for the margins (%d)" % rc)
+    return M, E
 
 
 MOMENT_NAMES = ("mean_m", "mean_abs_m", "mean_m2", "mean_m4", "mean_e", "mean_e2", "U4", "chi", "C")

@@ -282,6 +282,49 @@ void orc_run_window(int8_t *s, uint64_t L, uint64_t row0, uint64_t nrows, uint64
 }
 
 /* ------------------------------------------------------------------------ */
+/* M and E of a whole periodic lattice after each of its first k sweeps from */
+/* a cold start (all +1 when up != 0, else all -1), computed tile by tile so  */
+/* that the lattice is never held in memory: a tile of R rows is simulated as */
+/* a light-cone window with a margin of 2k + 1 rows on each side, and after   */
+/* every sweep the tile's own rows (exact, the margin has not reached them)   */
+/* give their spins, their horizontal bonds and their bonds to the next row.  */
+/* M[j], E[j] receive the values after sweep j (j = 0 .. k-1).                */
+/* ------------------------------------------------------------------------ */
+int orc_cold_tiled_counts(uint64_t L, int up, uint64_t k, uint64_t tile_rows, uint64_t seed,
+                          uint32_t stream_id, uint32_t thr4, uint32_t thr8, int64_t *M, int64_t *E)
+{
+    const uint64_t margin = 2 * k + 1;
+    if (tile_rows == 0 || L % tile_rows != 0 || tile_rows + 2 * margin > L) return -1;
+    const uint64_t wrows = tile_rows + 2 * margin;
+    int8_t *w = (int8_t *)malloc(wrows * L);
+    if (!w) return -2;
+    for (uint64_t j = 0; j < k; ++j) M[j] = E[j] = 0;
+    for (uint64_t t0 = 0; t0 < L; t0 += tile_rows) {
+        const uint64_t row0 = (t0 + L - margin) % L;
+        orc_init_cold(w, wrows * L, up ? 1 : -1);
+        for (uint64_t j = 0; j < k; ++j) {
+            for (uint32_t p = 0; p < 2; ++p)
+                orc_half_sweep(w, L, row0, wrows, 0, j, p, seed, stream_id, thr4, thr8, 0, 0);
+            int64_t m = 0, e = 0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : m, e) schedule(static)
+#endif
+            for (uint64_t r = margin; r < margin + tile_rows; ++r) {
+                for (uint64_t x = 0; x < L; ++x) {
+                    int v = w[r * L + x];
+                    m += v;
+                    e -= v * (w[r * L + (x + 1) % L] + w[(r + 1) * L + x]);
+                }
+            }
+            M[j] += m;
+            E[j] += e;
+        }
+    }
+    free(w);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* FP64 observables from integer samples, plain summation in sample order.    */
 /* m = M/N, e = E/N over samples [burn, n):                                   */
 /*   out[0] <m>   out[1] <|m|>  out[2] <m^2>  out[3] <m^4>                    */

@@ -59,3 +59,11 @@ def lattice_kwargs(spec: dict) -> dict:
     """The Lattice(...) arguments of a workload entry."""
     keys = ("L", "T", "seed", "stream_id", "init", "word_bits")
     return {k: spec[k] for k in keys if k in spec}
+
+
+def onsager_m0(T: float) -> float:
+    """Onsager's spontaneous magnetisation per spin, (1 - sinh(2/T)^-4)^(1/8) below T_c
+    (the reference the L = 524288 workload is compared with)."""
+    if T >= TC_EXACT:
+        return 0.0
+    return (1.0 - math.sinh(2.0 / T) ** -4) ** 0.125

@@ -1,0 +1,56 @@
+"""The largest single-GPU lattice: L = 524288 (2^38 spins, 64-bit words, 32 GiB),
+cold start, T = 2.0, seed 5, 200 sweeps, M and E every sweep.
+
+Checked at full size: rows of three windows after 5 sweeps against the oracle's
+light-cone evolution of the same rows (the wrap-around rows included), the
+fused M/E against a GPU recount, and the magnetisation per spin over sweeps
+100-200 against Onsager's spontaneous magnetisation (1 - sinh(2/T)^-4)^(1/8).
+The whole-lattice M/E of the first 5 sweeps against the oracle (tile by tile,
+about a quarter of an hour of host CPU) runs when ISING_FULL_ORACLE=1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import exact
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1007_3726_gb300 as P
+
+    P.build()
+    P.load()
+    return P
+
+
+def test_largest_lattice_L524288(P, orc):
+    import torch
+
+    free, _ = torch.cuda.mem_get_info()
+    if free < 40 * 2 ** 30:
+        pytest.skip("needs 40 GiB of free device memory")
+    L, T, seed, k = 524288, 2.0, 5, 5
+    thr4, thr8 = orc.thresholds(T)
+    lat = P.Lattice(L, T, seed=seed, init="cold_up", word_bits=64)
+    M5, E5 = lat.sweep(k, 1, collect=True)
+    margin = 2 * k + 1
+    for row0 in (0, L // 2 + 17, L - 40):
+        w = np.ones((64 + 2 * margin, L), dtype=np.int8)
+        orc.run_window(w, L, (row0 - margin) % L, k, seed, 0, thr4, thr8)
+        assert np.array_equal(lat.spins(row0, 64), w[margin:margin + 64]), row0
+    assert (int(M5[-1]), int(E5[-1])) == lat.recount()
+    if os.environ.get("ISING_FULL_ORACLE") == "1":
+        Mo, Eo = orc.cold_tiled_counts(L, k, seed, 0, thr4, thr8, up=True, tile_rows=4096)
+        assert np.array_equal(M5, Mo) and np.array_equal(E5, Eo)
+    M, E = lat.sweep(200 - k, 1, collect=True)
+    d = lat.measure()
+    assert d["sweeps_done"] == 200 and (d["M"], d["E"]) == lat.recount()
+    N = float(L) * L
+    m = np.abs(M[100 - k:]) / N
+    assert abs(m.mean() - exact.onsager_m0(T)) < 1e-3, m.mean()
+    # the energy per spin approaches Onsager's u(T) as well (finite time, looser)
+    assert abs(E[-1] / N - exact.onsager_u(T)) < 5e-3

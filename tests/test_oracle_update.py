@@ -212,3 +212,14 @@ def test_onsager_closed_forms_against_finite_lattices():
         m6 = exact.transfer_averages(6, T)["mean_abs_m"]
         assert abs(m6 - exact.onsager_m0(T)) < 5e-3
     assert exact.onsager_m0(3.0) == 0.0
+
+
+def test_cold_tiled_counts_equal_whole_lattice_run(orc):
+    """The tile-by-tile light-cone counts equal a run of the whole lattice."""
+    for L, T, k, tile in ((64, 2.0, 3, 16), (128, TC, 4, 64), (96, 3.0, 2, 32)):
+        thr4, thr8 = orc.thresholds(T)
+        for up in (True, False):
+            s = orc.init_cold(L, 1 if up else -1)
+            M, E = orc.run(s, k, seed=5, stream_id=3, thr4=thr4, thr8=thr8)
+            Mt, Et = orc.cold_tiled_counts(L, k, 5, 3, thr4, thr8, up=up, tile_rows=tile)
+            assert np.array_equal(M, Mt) and np.array_equal(E, Et)
