@@ -68,7 +68,8 @@ typedef enum {
     ISING_ERR_OOM = 2,     /* device or pinned host allocation failed */
     ISING_ERR_CUDA = 3,    /* a CUDA call failed; the handle is now failed */
     ISING_ERR_TIMEOUT = 4, /* a bounded device wait expired; the handle is now failed */
-    ISING_ERR_STATE = 5    /* the handle failed earlier; only ising_destroy is allowed */
+    ISING_ERR_STATE = 5,   /* the handle failed earlier; only ising_destroy is allowed */
+    ISING_ERR_CANCELLED = 6 /* a served request was cancelled before it finished */
 } ising_status;
 
 typedef enum {
@@ -263,6 +264,64 @@ ISING_API ising_status ising_batch_tune(ising_lattice *const *hs, uint32_t n, co
 /* One run of a batch made with default options, then destroyed. */
 ISING_API ising_status ising_sweep_batch(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
                                          uint32_t record_every);
+
+/* ---- request server: continuous batching --------------------------------- */
+
+/*
+ * A server accepts simulation requests at any time from any thread.  A worker
+ * thread admits them in arrival order while their device memory fits the
+ * budget; admitted lattices stay resident.  Each launch is one persistent
+ * batch (above) over the resident lattices that fit it, each advancing by up
+ * to epoch_sweeps sweeps; the lattices that ran go behind those that waited
+ * (round robin), finished requests leave and free their memory, and new ones
+ * join at the next launch.  A request's samples and final state are exactly
+ * those of ising_sweep on the same parameters alone.
+ */
+typedef struct ising_server ising_server;
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* device memory of resident lattices (0 = 64 GiB) */
+    uint32_t epoch_sweeps;      /* sweeps per lattice per launch at most (0 = 1000) */
+    uint32_t max_active;        /* lattices per launch at most (0 = as shared memory allows) */
+    uint32_t keep_samples;      /* 1: keep each request's M/E samples for ising_server_samples */
+    ising_batch_opts batch;     /* launch options (block 0 = 256 threads, 4 CTAs per SM) */
+} ising_server_opts;
+typedef struct {
+    ising_params params;        /* FROM_BUFFER / FROM_PACKED data must stay valid until admission */
+    uint64_t nsweeps;           /* 1 .. 2^32 - 2 */
+    uint32_t record_every;
+    uint64_t tag;               /* returned in the result */
+} ising_request;
+typedef struct {
+    uint64_t id, tag;
+    ising_status status;        /* ISING_OK; ISING_ERR_OOM if larger than the budget;
+                                   ISING_ERR_CANCELLED; or why the launch failed */
+    ising_obs obs;              /* final counters and moments of all its samples */
+    double t_submit, t_admit, t_first_run, t_finish;  /* seconds since the server started */
+    uint64_t epochs;            /* launches it took part in */
+} ising_result;
+typedef struct {
+    uint64_t submitted, admitted, completed, failed, cancelled, queued, resident;
+    uint64_t epochs, mem_used, peak_mem, attempts;
+    double busy_seconds;        /* time inside launches */
+    double now;                 /* seconds since the server started */
+} ising_server_counters;
+
+/* Starts a server (and its worker thread) on the current device. */
+ISING_API ising_status ising_server_create(const ising_server_opts *opts, ising_server **out);
+/* Queues a request (thread-safe, does not block on the GPU); *id identifies it. */
+ISING_API ising_status ising_server_submit(ising_server *s, const ising_request *req, uint64_t *id);
+/* Cancels a queued or running request; a running one stops at its next launch boundary. */
+ISING_API ising_status ising_server_cancel(ising_server *s, uint64_t id);
+/* Takes up to cap finished results, waiting up to wait_s seconds for the first. */
+ISING_API ising_status ising_server_poll(ising_server *s, ising_result *out, uint32_t cap, uint32_t *n,
+                                         double wait_s);
+/* With keep_samples: the M/E samples of a polled, finished request (M or E NULL
+ * queries *n); taking them releases them. */
+ISING_API ising_status ising_server_samples(ising_server *s, uint64_t id, int64_t *M, int64_t *E,
+                                            uint64_t cap, uint64_t *n);
+ISING_API ising_status ising_server_stats(ising_server *s, ising_server_counters *out);
+/* Stops the worker; unfinished requests are dropped. */
+ISING_API ising_status ising_server_destroy(ising_server *s);
 
 /*
  * ising_sweep_noalloc - the sweep for callers that cannot allocate memory.

@@ -23,13 +23,13 @@ __all__ = [
     "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
     "ising_device_spins", "ising_sweep_noalloc", "ising_get_launch", "ising_set_launch",
-    "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "IsingBatchOpts",
+    "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "Server", "IsingBatchOpts",
     "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
 
-OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(6)
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_CANCELLED = range(7)
 STATUS_NAMES = {0: "ISING_OK", 1: "ISING_ERR_INVALID", 2: "ISING_ERR_OOM", 3: "ISING_ERR_CUDA",
-                4: "ISING_ERR_TIMEOUT", 5: "ISING_ERR_STATE"}
+                4: "ISING_ERR_TIMEOUT", 5: "ISING_ERR_STATE", 6: "ISING_ERR_CANCELLED"}
 INIT_MODES = {"cold_up": 0, "cold": 0, "cold_down": 1, "hot": 2, "buffer": 3, "packed": 4}
 
 
@@ -71,6 +71,39 @@ class IsingBatchOpts(ctypes.Structure):
                 ("rows_per_item", ctypes.c_uint32), ("insert", ctypes.c_uint32),
                 ("use_graph", ctypes.c_uint32), ("wait_ms", ctypes.c_double),
                 ("hold_strip", ctypes.c_uint32)]
+
+
+class IsingServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("epoch_sweeps", ctypes.c_uint32),
+                ("max_active", ctypes.c_uint32), ("keep_samples", ctypes.c_uint32),
+                ("batch", IsingBatchOpts)]
+
+
+class IsingRequest(ctypes.Structure):
+    _fields_ = [("params", IsingParams), ("nsweeps", ctypes.c_uint64), ("record_every", ctypes.c_uint32),
+                ("tag", ctypes.c_uint64)]
+
+
+class IsingResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("obs", IsingObs), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_first_run", ctypes.c_double), ("t_finish", ctypes.c_double),
+                ("epochs", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "obs"}
+        d["obs"] = self.obs.as_dict()
+        return d
+
+
+class IsingServerCounters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "admitted", "completed", "failed",
+                                                 "cancelled", "queued", "resident", "epochs",
+                                                 "mem_used", "peak_mem", "attempts")] + \
+               [("busy_seconds", ctypes.c_double), ("now", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -122,6 +155,14 @@ def load(path: str | None = None):
         "ising_sweep_batch": ([ctypes.POINTER(H), ctypes.c_uint32, _u64p, ctypes.c_uint32], ctypes.c_int),
         "ising_batch_tune": ([ctypes.POINTER(H), ctypes.c_uint32, _u64p, ctypes.c_uint32,
                               ctypes.POINTER(IsingBatchOpts), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "ising_server_create": ([ctypes.POINTER(IsingServerOpts), ctypes.POINTER(H)], ctypes.c_int),
+        "ising_server_submit": ([H, ctypes.POINTER(IsingRequest), _u64p], ctypes.c_int),
+        "ising_server_cancel": ([H, ctypes.c_uint64], ctypes.c_int),
+        "ising_server_poll": ([H, ctypes.POINTER(IsingResult), ctypes.c_uint32, _u32p, ctypes.c_double],
+                              ctypes.c_int),
+        "ising_server_samples": ([H, ctypes.c_uint64, _i64p, _i64p, ctypes.c_uint64, _u64p], ctypes.c_int),
+        "ising_server_stats": ([H, ctypes.POINTER(IsingServerCounters)], ctypes.c_int),
+        "ising_server_destroy": ([H], ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
@@ -304,6 +345,67 @@ class Batch:
         if self._b is not None and self._b.value:
             load().ising_batch_destroy(self._b)
         self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Request server with continuous batching (ising_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, epoch_sweeps: int = 0, max_active: int = 0,
+                 keep_samples: bool = False, **batch_opts):
+        o = IsingServerOpts(hbm_budget_bytes=hbm_budget_bytes, epoch_sweeps=epoch_sweeps,
+                            max_active=max_active, keep_samples=1 if keep_samples else 0,
+                            batch=IsingBatchOpts(**batch_opts))
+        self._s = ctypes.c_void_p()
+        _check(load().ising_server_create(ctypes.byref(o), ctypes.byref(self._s)))
+
+    def submit(self, L: int, T: float, nsweeps: int, seed: int = 0, stream_id: int = 0, init: str = "hot",
+               record_every: int = 0, word_bits: int = 0, tag: int = 0) -> int:
+        p = IsingParams(L=L, T=T, seed=seed, stream_id=stream_id, init=INIT_MODES[init], init_data=None,
+                        word_bits=word_bits)
+        r = IsingRequest(params=p, nsweeps=nsweeps, record_every=record_every, tag=tag)
+        rid = ctypes.c_uint64()
+        _check(load().ising_server_submit(self._s, ctypes.byref(r), ctypes.byref(rid)))
+        return rid.value
+
+    def cancel(self, rid: int):
+        _check(load().ising_server_cancel(self._s, rid))
+
+    def poll(self, cap: int = 256, wait_s: float = 0.0) -> list[dict]:
+        arr = (IsingResult * cap)()
+        n = ctypes.c_uint32()
+        _check(load().ising_server_poll(self._s, arr, cap, ctypes.byref(n), wait_s))
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def samples(self, rid: int):
+        n = ctypes.c_uint64()
+        _check(load().ising_server_samples(self._s, rid, None, None, 0, ctypes.byref(n)))
+        M = np.zeros(max(n.value, 1), dtype=np.int64)
+        E = np.zeros(max(n.value, 1), dtype=np.int64)
+        _check(load().ising_server_samples(self._s, rid, M.ctypes.data_as(_i64p), E.ctypes.data_as(_i64p),
+                                           n.value, ctypes.byref(n)))
+        return M[:n.value], E[:n.value]
+
+    def stats(self) -> dict:
+        o = IsingServerCounters()
+        _check(load().ising_server_stats(self._s, ctypes.byref(o)))
+        return o.as_dict()
+
+    def close(self):
+        if self._s is not None and self._s.value:
+            load().ising_server_destroy(self._s)
+        self._s = None
 
     def __del__(self):
         try:

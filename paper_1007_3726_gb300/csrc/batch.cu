@@ -13,6 +13,7 @@
 // launch sets an error flag and returns.  The arithmetic of a site update is
 // the same device code as the one-lattice kernel, so every lattice, sample and
 // final state is bit-identical to ising_sweep's.
+#include "batch_internal.h"
 #include "handle.h"
 #include "kernels.h"
 #include "runtime.h"
@@ -50,19 +51,6 @@ struct BatchStrip {
     RoundKeys key;
 };
 
-struct BatchLaunchArgs {
-    const BatchStrip *strips;
-    const uint32_t *cta_first;          // strips of CTA b: cta_strips[cta_first[b] .. cta_first[b + 1])
-    const uint32_t *cta_strips;
-    const uint32_t *t0;                 // first sweep index of each lattice in this launch
-    uint32_t max_steps;
-    uint32_t rows_per_item;
-    uint32_t max_strips;                // table entries per CTA
-    uint32_t table_words;               // 64-bit words of the tables before the strips' rows
-    unsigned int *error_flag;           // set to 1 when a wait ran out
-    long long wait_cycles;              // clock limit of one wait
-    uint32_t hold_strip;                // 1 + index of a strip that never publishes (0 = none)
-};
 
 namespace {
 
@@ -407,40 +395,6 @@ BatchKernel batch_kernel(uint32_t insert)
 }  // namespace
 
 // ------------------------------------------------------------------ host ---
-struct ising_batch {
-    std::vector<ising_lattice *> hs;
-    std::vector<uint64_t> sweeps;           // per lattice per run
-    uint32_t record_every = 0;
-    ising_batch_opts opts{};
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    Allocator alloc;
-    // plan
-    std::vector<BatchStrip> strips;
-    std::vector<uint32_t> cta_first, cta_strips;
-    uint32_t grid = 0, block = 512, max_steps = 0, max_strips = 0, table_words = 0;
-    size_t smem_bytes = 0;
-    std::vector<size_t> sample_base;        // first slot of each lattice in the counters
-    std::vector<size_t> nrec;               // sample slots of each lattice per run (the most a run can record)
-    size_t slots = 0;                       // recorded slots + one final slot per lattice
-    // device memory
-    void *d_plan = nullptr;                 // strips, cta_first, cta_strips, t0
-    size_t plan_bytes = 0;
-    void *d_work = nullptr;                 // borders, progress, counters, error flag
-    size_t work_bytes = 0;
-    size_t off_progress = 0, off_counters = 0, off_error = 0, off_t0 = 0;
-    size_t progress_bytes = 0;
-    unsigned long long *h_counters = nullptr;  // pinned
-    uint32_t *h_t0 = nullptr;                  // pinned
-    unsigned int *h_error = nullptr;           // pinned
-    cudaEvent_t ev = nullptr;
-    bool own_stream = false;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    BatchLaunchArgs args{};
-    bool failed = false;
-};
-
 namespace {
 
 // Bytes of the per-strip tables at the start of the kernel's shared memory.
@@ -475,21 +429,21 @@ void free_batch(ising_batch *b)
 
 // Splits every lattice into strips and assigns them to CTAs (largest work
 // first, to the least loaded CTA with room in shared memory).
-ising_status make_plan(ising_batch *b)
+// CTAs of a plan and the dynamic shared memory each can give to strips.
+void plan_budget(const ising_batch *b, uint32_t *P_out, size_t *smem_cta_out)
 {
-    int dev = b->device;
+    const int dev = b->device;
     int sms = 0, smem_optin = 0, smem_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (sms <= 0) return fail(ISING_ERR_CUDA, "no multiprocessors");
-    b->block = b->opts.block ? b->opts.block : 512;
+    const uint32_t block = b->opts.block ? b->opts.block : 512;
     uint32_t ctas_per_sm = b->opts.ctas_per_sm ? b->opts.ctas_per_sm : 2;
     {
         // no more CTAs per SM than the registers allow
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->opts.insert), (int)b->opts.block
-                                                              ? (int)b->opts.block : 512, 0) == cudaSuccess &&
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->opts.insert), (int)block, 0) ==
+                cudaSuccess &&
             occ > 0)
             ctas_per_sm = std::min<uint32_t>(ctas_per_sm, (uint32_t)occ);
     }
@@ -503,8 +457,17 @@ ising_status make_plan(ising_batch *b)
     smem_cta = std::min<size_t>(smem_cta, (size_t)smem_optin > fa.sharedSizeBytes
                                               ? (size_t)smem_optin - fa.sharedSizeBytes
                                               : 0);
-    const uint32_t P = (uint32_t)sms * ctas_per_sm;
+    *P_out = (uint32_t)(sms > 0 ? sms : 1) * ctas_per_sm;
+    *smem_cta_out = smem_cta;
+}
 
+ising_status make_plan(ising_batch *b)
+{
+    b->block = b->opts.block ? b->opts.block : 512;
+    uint32_t P = 0;
+    size_t smem_cta = 0;
+    plan_budget(b, &P, &smem_cta);
+    if (P == 0 || smem_cta == 0) return fail(ISING_ERR_CUDA, "no multiprocessors or shared memory");
     const size_t n = b->hs.size();
     double total = 0;
     for (size_t i = 0; i < n; ++i) total += (double)b->hs[i]->L * b->hs[i]->L * b->sweeps[i];
@@ -626,7 +589,8 @@ ising_status make_plan(ising_batch *b)
         const uint64_t t0 = h->sweeps_done, ns = b->sweeps[i];
         (void)t0;
         // at most ceil(ns / record_every) samples in any run of ns sweeps
-        b->nrec[i] = b->record_every ? (ns + b->record_every - 1) / b->record_every : 0;
+        const uint64_t re = b->record_every[i];
+        b->nrec[i] = re ? (ns + re - 1) / re : 0;
         b->sample_base[i] = slot;
         slot += b->nrec[i] + 1;  // + the final slot
         b->max_steps = std::max<uint32_t>(b->max_steps, (uint32_t)(2 * ns));
@@ -646,7 +610,7 @@ ising_status make_plan(ising_batch *b)
         st.nstrips_lat = G;
         st.lat_index = q.lat;
         st.nsteps = (uint32_t)(2 * b->sweeps[q.lat]);
-        st.record_every = b->record_every;
+        st.record_every = b->record_every[q.lat];
         st.thr4 = h->thr4;
         st.thr8 = h->thr8;
         st.c3base = h->stream_id << 1;
@@ -694,13 +658,41 @@ ising_status alloc_batch(ising_batch *b)
     w += 256;
     b->work_bytes = w;
 
-    b->d_plan = b->alloc.allocate(b->plan_bytes, b->stream);
-    b->d_work = b->alloc.allocate(b->work_bytes, b->stream);
+    // reuse the buffers of an earlier plan when they are large enough
+    auto grow = [](size_t need, size_t cap) { return need <= cap ? cap : std::max(need, cap + cap / 2); };
+    if (b->plan_bytes > b->plan_cap) {
+        cudaStreamSynchronize(b->stream);
+        b->alloc.release(b->d_plan, b->stream);
+        b->plan_cap = grow(b->plan_bytes, b->plan_cap);
+        b->d_plan = b->alloc.allocate(b->plan_cap, b->stream);
+        if (!b->d_plan) b->plan_cap = 0;
+    }
+    if (b->work_bytes > b->work_cap) {
+        cudaStreamSynchronize(b->stream);
+        b->alloc.release(b->d_work, b->stream);
+        b->work_cap = grow(b->work_bytes, b->work_cap);
+        b->d_work = b->alloc.allocate(b->work_cap, b->stream);
+        if (!b->d_work) b->work_cap = 0;
+    }
     if (!b->d_plan || !b->d_work) return fail(ISING_ERR_OOM, "cannot allocate the batch plan");
-    if (cudaHostAlloc((void **)&b->h_counters, b->slots * 16, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&b->h_t0, std::max<size_t>(n, 1) * 4, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&b->h_error, 16, cudaHostAllocDefault) != cudaSuccess) {
+    bool host_ok = true;
+    if (b->slots > b->counters_cap) {
+        if (b->h_counters) cudaFreeHost(b->h_counters);
+        b->h_counters = nullptr;
+        b->counters_cap = grow(b->slots, b->counters_cap);
+        host_ok = cudaHostAlloc((void **)&b->h_counters, b->counters_cap * 16, cudaHostAllocDefault) == cudaSuccess;
+    }
+    if (host_ok && std::max<size_t>(n, 1) > b->t0_cap) {
+        if (b->h_t0) cudaFreeHost(b->h_t0);
+        b->h_t0 = nullptr;
+        b->t0_cap = grow(std::max<size_t>(n, 1), b->t0_cap);
+        host_ok = cudaHostAlloc((void **)&b->h_t0, b->t0_cap * 4, cudaHostAllocDefault) == cudaSuccess;
+    }
+    if (host_ok && !b->h_error) host_ok = cudaHostAlloc((void **)&b->h_error, 16, cudaHostAllocDefault) == cudaSuccess;
+    if (!host_ok) {
         cudaGetLastError();
+        b->counters_cap = b->h_counters ? b->counters_cap : 0;
+        b->t0_cap = b->h_t0 ? b->t0_cap : 0;
         return fail(ISING_ERR_OOM, "cannot allocate pinned host memory for the batch");
     }
     char *work = static_cast<char *>(b->d_work);
@@ -793,6 +785,81 @@ cudaError_t enqueue_run(ising_batch *b)
 
 }  // namespace
 
+namespace ising {
+
+ising_status batch_new(int device, const ising_batch_opts *opts, ising_batch **out)
+{
+    *out = nullptr;
+    ising_batch *b = new (std::nothrow) ising_batch();
+    if (!b) return fail(ISING_ERR_OOM, "host allocation failed");
+    if (opts) b->opts = *opts;
+    if (b->opts.block != 0 && b->opts.block != 256 && b->opts.block != 512) {
+        delete b;
+        return fail(ISING_ERR_INVALID, "block must be 256 or 512");
+    }
+    if (b->opts.insert > 2 || b->opts.rows_per_item > 64) {
+        delete b;
+        return fail(ISING_ERR_INVALID, "bad batch options");
+    }
+    b->device = device;
+    b->alloc = current_allocator();
+    // a stream of the batch's own (the legacy default stream cannot be captured)
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(ISING_ERR_CUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return fail(ISING_ERR_CUDA, "event creation failed");
+    }
+    *out = b;
+    return ISING_OK;
+}
+
+ising_status batch_replan(ising_batch *b, const std::vector<ising_lattice *> &hs,
+                          const std::vector<uint64_t> &sweeps, const std::vector<uint32_t> &record_every)
+{
+    if (b->failed) return fail(ISING_ERR_STATE, "batch failed earlier");
+    const size_t n = hs.size();
+    if (n == 0 || sweeps.size() != n || record_every.size() != n)
+        return fail(ISING_ERR_INVALID, "empty batch");
+    for (size_t i = 0; i < n; ++i) {
+        ising_status st = check_live(hs[i]);
+        if (st != ISING_OK) return st;
+        if (hs[i]->device != b->device) return fail(ISING_ERR_INVALID, "handles on different devices");
+        if (sweeps[i] == 0 || sweeps[i] > (1u << 30))
+            return fail(ISING_ERR_INVALID, "sweeps per run must be in [1, 2^30]");
+        if ((st = harvest(hs[i])) != ISING_OK) return st;
+    }
+    cudaStreamSynchronize(b->stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+    b->hs = hs;
+    b->sweeps = sweeps;
+    b->record_every = record_every;
+    ising_status st = make_plan(b);
+    if (st == ISING_OK) st = alloc_batch(b);
+    if (st != ISING_OK) b->hs.clear();
+    return st;
+}
+
+void batch_free(ising_batch *b) { free_batch(b); }
+
+size_t batch_capacity_bytes(ising_batch *b)
+{
+    uint32_t P = 0;
+    size_t smem_cta = 0;
+    plan_budget(b, &P, &smem_cta);
+    return (size_t)P * smem_cta;
+}
+
+}  // namespace ising
+
 extern "C" {
 
 ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
@@ -806,50 +873,19 @@ ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, 
     for (uint32_t i = 0; i < n; ++i) {
         ising_status st = check_live(hs[i]);
         if (st != ISING_OK) return st;
-        if (hs[i]->device != hs[0]->device) return fail(ISING_ERR_INVALID, "handles on different devices");
-        if (nsweeps[i] == 0 || nsweeps[i] > (1u << 30))
-            return fail(ISING_ERR_INVALID, "sweeps per run must be in [1, 2^30]");
         for (uint32_t k = 0; k < i; ++k)
             if (hs[k] == hs[i]) return fail(ISING_ERR_INVALID, "a handle appears twice");
     }
-    ising_batch *b = new (std::nothrow) ising_batch();
-    if (!b) return fail(ISING_ERR_OOM, "host allocation failed");
-    b->hs.assign(hs, hs + n);
-    b->sweeps.assign(nsweeps, nsweeps + n);
-    b->record_every = record_every;
-    if (opts) b->opts = *opts;
-    b->device = hs[0]->device;
-    b->alloc = current_allocator();
-    // a stream of the batch's own (the legacy default stream cannot be captured)
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        delete b;
-        return fail(ISING_ERR_CUDA, "stream creation failed");
-    }
-    b->own_stream = true;
-    if (b->opts.block != 0 && b->opts.block != 256 && b->opts.block != 512) {
-        delete b;
-        return fail(ISING_ERR_INVALID, "block must be 256 or 512");
-    }
-    if (b->opts.insert > 2 || b->opts.rows_per_item > 64) {
-        delete b;
-        return fail(ISING_ERR_INVALID, "bad batch options");
-    }
-    auto bail = [&](ising_status s) {
+    ising_batch *b = nullptr;
+    ising_status st = batch_new(hs[0]->device, opts, &b);
+    if (st != ISING_OK) return st;
+    st = batch_replan(b, std::vector<ising_lattice *>(hs, hs + n), std::vector<uint64_t>(nsweeps, nsweeps + n),
+                      std::vector<uint32_t>(n, record_every));
+    if (st != ISING_OK) {
         std::string msg = ising_last_error();
-        b->hs.clear();  // do not fail the handles for a planning error
         free_batch(b);
-        fail(s, "%s", msg.c_str());
-        return s;
-    };
-    ising_status st;
-    for (ising_lattice *h : b->hs)
-        if ((st = harvest(h)) != ISING_OK) return bail(st);
-    if ((st = make_plan(b)) != ISING_OK) return bail(st);
-    if ((st = alloc_batch(b)) != ISING_OK) return bail(st);
-    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        return bail(fail(ISING_ERR_CUDA, "event creation failed"));
+        fail(st, "%s", msg.c_str());
+        return st;
     }
     *out = b;
     return ISING_OK;
@@ -860,6 +896,7 @@ ISING_API ising_status ising_batch_run(ising_batch *b, uint32_t runs)
     clear_error();
     if (!b) return fail(ISING_ERR_INVALID, "null batch");
     if (b->failed) return fail(ISING_ERR_STATE, "batch failed earlier");
+    if (b->hs.empty()) return fail(ISING_ERR_STATE, "batch has no plan");
     cudaError_t e = cudaSetDevice(b->device);
     if (e != cudaSuccess) return bfail(b, e, "cudaSetDevice");
     const size_t n = b->hs.size();
@@ -904,10 +941,8 @@ ISING_API ising_status ising_batch_run(ising_batch *b, uint32_t runs)
         for (size_t i = 0; i < n; ++i) {
             ising_lattice *h = b->hs[i];
             const unsigned long long *c = b->h_counters + 2 * b->sample_base[i];
-            const uint64_t t0 = h->sweeps_done;
-            const size_t got = b->record_every
-                                   ? (size_t)((t0 + b->sweeps[i]) / b->record_every - t0 / b->record_every)
-                                   : 0;
+            const uint64_t t0 = h->sweeps_done, re = b->record_every[i];
+            const size_t got = re ? (size_t)((t0 + b->sweeps[i]) / re - t0 / re) : 0;
             for (size_t k = 0; k < got; ++k) {
                 h->sM.push_back(to_M(h, c[2 * k]));
                 h->sE.push_back(to_E(h, c[2 * k + 1]));
