@@ -322,6 +322,34 @@ def run_largest(args):
     return 0
 
 
+def run_served(args):
+    """The served request stream: Poisson arrivals at 200 requests/s for 60 s (L
+    uniform on the powers of two 64..4096, T uniform in [1.5, 3.5], sweeps
+    log-uniform in [10^2, 10^5], per-request seeds), admitted against a 64 GB
+    budget, then 60 s to drain; and a sustainable-rate stream at 20 requests/s.
+    One JSON line with p50/p99 latency and aggregate attempts/ns."""
+    import paper_1007_3726_gb300 as P
+    from paper_1007_3726_gb300 import serve
+
+    runs = {}
+    for name, rate, dur, drain in (("offered_200_per_s", 200.0, 60.0, 60.0),
+                                   ("sustainable_20_per_s", 20.0, 60.0, 120.0)):
+        reqs = serve.poisson_requests(rate=rate, duration=dur, seed=4)
+        with P.Server(hbm_budget_bytes=64 * 10 ** 9, epoch_sweeps=1000) as srv:
+            runs[name] = serve.run_stream(srv, reqs, drain_s=drain)
+    main = runs["offered_200_per_s"]
+    line = {"metric": "served p50/p99 latency and aggregate spin-flip attempts/ns",
+            "value": main["server_attempts_per_ns"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": main["makespan_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "Poisson 200 req/s for 60 s, L in 64..4096 (powers of two), "
+                                   "T in [1.5, 3.5], sweeps log-uniform 1e2..1e5, budget 64 GB, "
+                                   "M/E every 10 sweeps, 60 s drain"},
+            "runs": runs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
@@ -488,6 +516,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "largest":
         return run_largest(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args, ws, rank, local)
 
 
