@@ -2,6 +2,7 @@
 
     python -m paper_1007_3726_gb300 --L 32768 --T 2.269185 --seed 7 --init hot \
         --sweeps 1000 --record-every 1 [--word-bits 32] [--time]
+    python -m paper_1007_3726_gb300 fss-batch --sweeps 10000   (128 lattices, one launch)
 """
 import argparse
 import json
@@ -9,7 +10,38 @@ import sys
 import time
 
 
+def fss_batch(argv):
+    """The 128-lattice finite-size-scaling batch in one persistent launch."""
+    ap = argparse.ArgumentParser(prog="python -m paper_1007_3726_gb300 fss-batch")
+    ap.add_argument("--sweeps", type=int, default=10000)
+    ap.add_argument("--record-every", type=int, default=10)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--ctas-per-sm", type=int, default=4)
+    ap.add_argument("--rows-per-item", type=int, default=4)
+    a = ap.parse_args(argv)
+
+    import paper_1007_3726_gb300 as P
+    from paper_1007_3726_gb300 import workloads as WL
+
+    P.load()
+    specs = WL.fss_batch(sweeps=a.sweeps, record_every=a.record_every)
+    lats = [P.Lattice(**WL.lattice_kwargs(sp)) for sp in specs]
+    t0 = time.perf_counter()
+    with P.Batch(lats, [a.sweeps] * len(lats), a.record_every, block=a.block, ctas_per_sm=a.ctas_per_sm,
+                 rows_per_item=a.rows_per_item) as b:
+        info = b.info()
+        b.run(1)
+    el = time.perf_counter() - t0
+    N = sum(sp["L"] ** 2 for sp in specs)
+    print(json.dumps({"lattices": len(lats), "sweeps": a.sweeps, "plan": info, "seconds": el,
+                      "attempts_per_ns": N * a.sweeps / el / 1e9}))
+    return 0
+
+
 def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
+    if argv and argv[0] == "fss-batch":
+        return fss_batch(argv[1:])
     ap = argparse.ArgumentParser(prog="python -m paper_1007_3726_gb300")
     ap.add_argument("--L", type=int, default=1024)
     ap.add_argument("--T", type=float, default=2.269185)
