@@ -350,6 +350,31 @@ def run_served(args):
     return 0
 
 
+def run_fss(args):
+    """Finite-size scaling: U4 crossings of L = 64, 128, 256, 512 in [2.24, 2.30]
+    after 2e5 sweeps (20 % dropped), against Onsager's T_c = 2/ln(1 + sqrt 2)."""
+    import math
+
+    from paper_1007_3726_gb300 import fss
+
+    t = time.perf_counter()
+    res = fss.run_fss(sweeps=args.fss_sweeps)
+    el = time.perf_counter() - t
+    cr = fss.crossings(res)
+    tc = 2.0 / math.log(1.0 + math.sqrt(2.0))
+    N = sum(L * L for L in res) * len(next(iter(res.values()))[0])
+    line = {"metric": "finite-size-scaling T_c from U4 crossings", "value": cr[-1]["T_cross"],
+            "unit": "T", "onsager_tc": tc, "crossings": cr, "seconds": el,
+            "attempts_per_ns": N * args.fss_sweeps / el / 1e9,
+            "U4": {str(L): [float(x) for x in v[1]] for L, v in res.items()},
+            "temps": [float(x) for x in next(iter(res.values()))[0]],
+            "config": {"workload": "L in {64,128,256,512} x 32 T in [2.24, 2.30], cold start, "
+                                   "%d sweeps, sample every 10, 20%% burn-in, block bootstrap"
+                                   % args.fss_sweeps}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
@@ -508,7 +533,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the L=64 and 128-lattice workloads")
-    ap.add_argument("--workload", default="default", choices=["default", "largest", "served"],
+    ap.add_argument("--fss-sweeps", type=int, default=200000)
+    ap.add_argument("--workload", default="default", choices=["default", "largest", "served", "fss"],
                     help="default: L=32768 (the benchmark line); largest: L=524288; served: request stream")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
@@ -518,6 +544,8 @@ def main():
         return run_largest(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "fss":
+        return run_fss(args)
     return run_ours(args, ws, rank, local)
 
 

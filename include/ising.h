@@ -150,6 +150,11 @@ ISING_API ising_status ising_get_spins(ising_lattice *h, uint64_t row0, uint64_t
  * storage layout above with the handle's word width).  Waits for the GPU. */
 ISING_API ising_status ising_get_packed(ising_lattice *h, void *out, size_t bytes);
 
+/* Copies recorded samples first .. first + count - 1 (fewer if fewer exist;
+ * *n_out tells how many) to the host arrays M and E.  Waits for the GPU. */
+ISING_API ising_status ising_get_samples(ising_lattice *h, uint64_t first, uint64_t count, int64_t *M,
+                                         int64_t *E, uint64_t *n_out);
+
 /* Full popcount recount of the current state on the GPU (independent of the
  * values fused into the sweep).  Waits for the GPU. */
 ISING_API ising_status ising_recount(ising_lattice *h, int64_t *M, int64_t *E);

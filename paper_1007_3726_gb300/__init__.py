@@ -20,7 +20,7 @@ from ._build import LIB_PATH, build  # noqa: F401
 
 __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
-    "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount",
+    "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount", "ising_get_samples",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
     "ising_device_spins", "ising_sweep_noalloc", "ising_get_launch", "ising_set_launch",
     "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "Server", "IsingBatchOpts",
@@ -136,6 +136,7 @@ def load(path: str | None = None):
         "ising_get_spins": ([H, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
         "ising_get_packed": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
         "ising_recount": ([H, _i64p, _i64p], ctypes.c_int),
+        "ising_get_samples": ([H, ctypes.c_uint64, ctypes.c_uint64, _i64p, _i64p, _u64p], ctypes.c_int),
         "ising_info": ([H, _u32p, _u64p, _u64p], ctypes.c_int),
         "ising_device_spins": ([H, _vpp, _szp], ctypes.c_int),
         "ising_thresholds": ([ctypes.c_double, _u32p, _u32p], ctypes.c_int),
@@ -239,6 +240,18 @@ def ising_get_spins(h, row0: int, nrows: int, out: np.ndarray):
 def ising_get_packed(h, out: np.ndarray):
     assert out.flags.c_contiguous
     _check(load().ising_get_packed(h, out.ctypes.data, out.nbytes))
+
+
+def ising_get_samples(h, first: int = 0, count: int | None = None):
+    """Recorded (M, E) samples first .. first + count - 1 as int64 arrays."""
+    if count is None:
+        count = ising_measure(h)["n_samples"] + 1
+    M = np.zeros(max(count, 1), dtype=np.int64)
+    E = np.zeros(max(count, 1), dtype=np.int64)
+    n = ctypes.c_uint64()
+    _check(load().ising_get_samples(h, first, count, M.ctypes.data_as(_i64p), E.ctypes.data_as(_i64p),
+                                    ctypes.byref(n)))
+    return M[:n.value], E[:n.value]
 
 
 def ising_recount(h) -> tuple[int, int]:
@@ -511,6 +524,10 @@ class Lattice:
 
     def recount(self) -> tuple[int, int]:
         return ising_recount(self._h)
+
+    def samples(self, first: int = 0, count: int | None = None):
+        """All (or some) recorded (M, E) samples of the lattice."""
+        return ising_get_samples(self._h, first, count)
 
     @property
     def launch(self) -> dict:

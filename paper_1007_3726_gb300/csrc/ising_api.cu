@@ -6,6 +6,7 @@
 #include "handle.h"
 #include "runtime.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -484,6 +485,24 @@ ising_status ising_recount(ising_lattice *h, int64_t *M, int64_t *E)
     CK(h, cudaStreamSynchronize(h->stream));
     *M = to_M(h, h->h_acc[0]);
     *E = to_E(h, h->h_acc[1]);
+    return ISING_OK;
+}
+
+ising_status ising_get_samples(ising_lattice *h, uint64_t first, uint64_t count, int64_t *M, int64_t *E,
+                               uint64_t *n_out)
+{
+    clear_error();
+    ising_status st = check_live(h);
+    if (st != ISING_OK) return st;
+    if ((st = harvest(h)) != ISING_OK) return st;
+    const uint64_t have = h->sM.size();
+    const uint64_t n = first >= have ? 0 : std::min<uint64_t>(count, have - first);
+    if (n_out) *n_out = n;
+    if (n && (!M || !E)) return fail(ISING_ERR_INVALID, "null output");
+    for (uint64_t i = 0; i < n; ++i) {
+        M[i] = h->sM[first + i];
+        E[i] = h->sE[first + i];
+    }
     return ISING_OK;
 }
 

@@ -186,3 +186,30 @@ def test_batch_tune_restores_lattices_and_results_stay_exact(P):
     with P.Batch(lats, sweeps, 1, **opts) as b:
         b.run(1)
     _check(P, lats, ref)
+
+
+def test_samples_round_trip(P, orc):
+    L, T = 128, 2.4
+    lat = P.Lattice(L, T, seed=4, init="hot")
+    lat.sweep(30, 2)
+    M, E = lat.samples()
+    s = orc.init_hot(L, 4)
+    thr4, thr8 = orc.thresholds(T)
+    Mo, Eo = orc.run(s, 30, 4, 0, thr4, thr8)
+    assert np.array_equal(M, Mo[1::2]) and np.array_equal(E, Eo[1::2])
+    M2, E2 = lat.samples(first=10, count=3)
+    assert np.array_equal(M2, M[10:13]) and np.array_equal(E2, E[10:13])
+
+
+def test_binder_crossing_small_lattices(P):
+    """The paper's correctness test in miniature: U4 curves of L = 64 and 128
+    cross near Onsager's T_c."""
+    import math
+
+    from paper_1007_3726_gb300 import fss
+
+    res = fss.run_fss(Ls=(64, 128), temps=np.linspace(2.20, 2.34, 8), sweeps=40000)
+    cr = fss.crossings(res)[0]
+    tc = 2.0 / math.log(1.0 + math.sqrt(2.0))
+    assert cr["T_cross"] is not None
+    assert abs(cr["T_cross"] - tc) < max(0.02, 5 * (cr["err"] or 0.0))
