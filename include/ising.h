@@ -328,6 +328,30 @@ ISING_API ising_status ising_server_stats(ising_server *s, ising_server_counters
 /* Stops the worker; unfinished requests are dropped. */
 ISING_API ising_status ising_server_destroy(ising_server *s);
 
+/* ---- one lattice over several GPUs: row strips ------------------------------ */
+
+/*
+ * The row-strip form of the super-lattice decomposition of Sec. 6.1: each rank
+ * holds global rows [row0, row0 + nrows) of an L x L lattice in a device
+ * buffer d_rows of (nrows + 2) rows in the storage layout above: a halo row
+ * (the global row above the strip), the strip, a halo row (the row below).
+ * Before every checkerboard step the caller fills the two halos with the
+ * neighbouring ranks' boundary rows ("copy neighbor borders to GPU memory",
+ * Sec. 6.1); ising_strip_step then updates the strip rows of parity p for
+ * sweep t with the same per-site Philox draws as the whole lattice, so the
+ * strips together equal ising_sweep bit for bit for any split.  With p == 1
+ * and d_counts (2 device counters) not NULL, the step adds the strip's +1
+ * spins and the anti-aligned bonds of its parity-1 sites after the step; the
+ * sums over all ranks give M = 2 up - L^2 and E = 2 anti - 2 L^2.  Neither
+ * call allocates memory; both are queued on cuda_stream.
+ */
+ISING_API ising_status ising_strip_init(void *d_rows, uint64_t L, uint32_t word_bits, uint64_t row0,
+                                        uint64_t nrows, ising_init init, uint64_t seed, uint32_t stream_id,
+                                        void *cuda_stream);
+ISING_API ising_status ising_strip_step(void *d_rows, uint64_t L, uint32_t word_bits, uint64_t row0,
+                                        uint64_t nrows, double T, uint64_t seed, uint32_t stream_id, uint32_t t,
+                                        uint32_t p, unsigned long long *d_counts, void *cuda_stream);
+
 /*
  * ising_sweep_noalloc - the sweep for callers that cannot allocate memory.
  * The paper has no counterpart; this entry point exists for callers that own

@@ -22,7 +22,7 @@ __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
     "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount", "ising_get_samples",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
-    "ising_device_spins", "ising_sweep_noalloc", "ising_get_launch", "ising_set_launch",
+    "ising_device_spins", "ising_sweep_noalloc", "ising_strip_init", "ising_strip_step", "ising_get_launch", "ising_set_launch",
     "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "Server", "IsingBatchOpts",
     "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
@@ -164,6 +164,13 @@ def load(path: str | None = None):
         "ising_server_samples": ([H, ctypes.c_uint64, _i64p, _i64p, ctypes.c_uint64, _u64p], ctypes.c_int),
         "ising_server_stats": ([H, ctypes.POINTER(IsingServerCounters)], ctypes.c_int),
         "ising_server_destroy": ([H], ctypes.c_int),
+        "ising_strip_init": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                              ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                              ctypes.c_void_p], ctypes.c_int),
+        "ising_strip_step": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                              ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                              ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p],
+                             ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
@@ -431,6 +438,18 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def ising_strip_init(d_rows: int, L: int, word_bits: int, row0: int, nrows: int, init: str = "hot",
+                     seed: int = 0, stream_id: int = 0, stream=None):
+    _check(load().ising_strip_init(d_rows, L, word_bits, row0, nrows, INIT_MODES[init], seed, stream_id,
+                                   _stream_ptr(stream)))
+
+
+def ising_strip_step(d_rows: int, L: int, word_bits: int, row0: int, nrows: int, T: float, seed: int,
+                     stream_id: int, t: int, p: int, d_counts: int | None = None, stream=None):
+    _check(load().ising_strip_step(d_rows, L, word_bits, row0, nrows, float(T), seed, stream_id, t, p,
+                                   d_counts, _stream_ptr(stream)))
 
 
 _alloc_keepalive = []

@@ -42,7 +42,7 @@ __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
     const uint64_t rows = a.rows;
     const uint32_t W = a.words_per_row;
     const uint32_t R = a.rows_per_item;
-    const uint32_t nrb = (uint32_t)(rows / R);
+    const uint32_t nrb = (uint32_t)(a.update_rows / R);
     const uint64_t groups_per_row = a.L >> 3;
 
     unsigned int cnt_up = 0, cnt_anti = 0;
@@ -52,12 +52,13 @@ __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
     while (rb < nrb) {
         const int64_t dl = (w == 0) ? (int64_t)W - 1 : -1;  // to the left neighbour word
         const int64_t dr = (w + 1 == W) ? 1 - (int64_t)W : 1;
-        const uint64_t y0 = (uint64_t)rb * R;
+        const uint64_t y0 = a.first_row + (uint64_t)rb * R;   // buffer row
+        const uint64_t yg = (uint64_t)(a.y_offset + (int64_t)y0);  // global row
         Word *p = S + y0 * W + w;
         Word up = *((y0 == 0) ? S + (rows - 1) * W + w : p - W);
         Word cur = *p;
-        uint64_t g = y0 * groups_per_row + (uint64_t)w * NB;
-        uint32_t off = (uint32_t)((y0 + a.p) & 1u);  // parity of the target bit positions
+        uint64_t g = yg * groups_per_row + (uint64_t)w * NB;
+        uint32_t off = (uint32_t)((yg + a.p) & 1u);  // parity of the target bit positions
         for (uint32_t r = 0; r < R; ++r) {
             Word *const pn = (y0 + r + 1 == rows) ? S + w : p + W;
             const Word dn = *pn;
@@ -99,12 +100,12 @@ __global__ void __launch_bounds__(512, 4) k_half_sweep_r32(const __grid_constant
 }
 
 template <typename Word>
-__global__ void k_init_hot(Word *S, uint64_t nwords, uint64_t L, RoundKeys key, uint32_t c3)
+__global__ void k_init_hot(Word *S, uint64_t nwords, uint64_t first_word, RoundKeys key, uint32_t c3)
 {
     constexpr int B = WordTraits<Word>::bits;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t n0 = i * B;  // first site of the word (row-major site index)
+        const uint64_t n0 = (first_word + i) * B;  // first site of the word (row-major site index)
         uint32_t x0 = (uint32_t)(n0 >> 7), x1 = (uint32_t)(n0 >> 39), x2 = 0xFFFFFFFFu, x3 = c3;
         philox_rounds(x0, x1, x2, x3, key);
         const uint32_t o[4] = {x0, x1, x2, x3};
@@ -284,7 +285,12 @@ int resolve_grid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 
 cudaError_t launch_half_sweep(HalfSweepArgs a, const LaunchConfig &c, cudaStream_t s)
 {
-    const int grid = resolve_grid(c, a.L, a.rows);
+    if (a.update_rows == 0) {  // a whole periodic lattice
+        a.first_row = 0;
+        a.update_rows = a.rows;
+        a.y_offset = 0;
+    }
+    const int grid = resolve_grid(c, a.L, a.update_rows);
     a.words_per_row = (uint32_t)(a.L / c.proc_bits);
     a.rows_per_item = c.rows_per_item;
     a.zero = 0u;
@@ -300,9 +306,23 @@ cudaError_t launch_init_hot(void *spins, uint64_t L, uint32_t word_bits, uint64_
     const uint64_t nwords = L * (L / word_bits);
     const int block = 256, grid = grid_for(nwords, block, 8);
     if (word_bits == 64)
-        k_init_hot<uint64_t><<<grid, block, 0, s>>>((uint64_t *)spins, nwords, L, k, stream_id << 1);
+        k_init_hot<uint64_t><<<grid, block, 0, s>>>((uint64_t *)spins, nwords, 0, k, stream_id << 1);
     else
-        k_init_hot<uint32_t><<<grid, block, 0, s>>>((uint32_t *)spins, nwords, L, k, stream_id << 1);
+        k_init_hot<uint32_t><<<grid, block, 0, s>>>((uint32_t *)spins, nwords, 0, k, stream_id << 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_hot_rows(void *spins, uint64_t L, uint32_t word_bits, uint64_t row0,
+                                 uint64_t nrows, uint64_t seed, uint32_t stream_id, cudaStream_t s)
+{
+    const RoundKeys k = make_round_keys(seed);
+    const uint64_t W = L / word_bits;
+    const uint64_t nwords = nrows * W;
+    const int block = 256, grid = grid_for(nwords, block, 8);
+    if (word_bits == 64)
+        k_init_hot<uint64_t><<<grid, block, 0, s>>>((uint64_t *)spins, nwords, row0 * W, k, stream_id << 1);
+    else
+        k_init_hot<uint32_t><<<grid, block, 0, s>>>((uint32_t *)spins, nwords, row0 * W, k, stream_id << 1);
     return cudaGetLastError();
 }
 

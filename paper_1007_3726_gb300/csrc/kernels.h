@@ -21,7 +21,10 @@ RoundKeys make_round_keys(uint64_t seed);
 struct HalfSweepArgs {
     void *spins;              // rows x words_per_row processing words (32- or 64-bit)
     uint64_t L;               // row length in sites (the lattice is L x L)
-    uint64_t rows;            // rows in the buffer (== L; fewer only for timing runs)
+    uint64_t rows;            // rows in the buffer (== L for a whole lattice)
+    uint64_t first_row;       // first buffer row updated (1 for a strip with a halo row above)
+    uint64_t update_rows;     // rows updated (== rows for a whole periodic lattice)
+    int64_t y_offset;         // global row index of buffer row 0 (Philox counters, parity)
     uint32_t words_per_row;   // L / processing bits
     uint32_t rows_per_item;   // rows one thread walks down (divides rows)
     RoundKeys key;
@@ -70,6 +73,9 @@ cudaError_t launch_half_sweep(HalfSweepArgs a, const LaunchConfig &c, cudaStream
 // Hot start (Philox with counter word 2 = 0xFFFFFFFF), cold start is a memset.
 cudaError_t launch_init_hot(void *spins, uint64_t L, uint32_t word_bits, uint64_t seed,
                             uint32_t stream_id, cudaStream_t s);
+// The hot start of global rows row0 .. row0 + nrows - 1 only, into `spins`.
+cudaError_t launch_init_hot_rows(void *spins, uint64_t L, uint32_t word_bits, uint64_t row0,
+                                 uint64_t nrows, uint64_t seed, uint32_t stream_id, cudaStream_t s);
 
 // int8 +1/-1 -> packed; *bad counts entries that are neither +1 nor -1.
 cudaError_t launch_pack(const int8_t *src, void *spins, uint64_t L, uint32_t word_bits,
