@@ -62,6 +62,21 @@ std::vector<LaunchConfig> launch_candidates(uint64_t L, uint64_t rows)
                         LaunchConfig c{pb, rc, ins, blk, R, 0};
                         if (launch_config_valid(c, L, rows)) out.push_back(c);
                     }
+    // larger grids than the resident one (the block scheduler evens out the tail):
+    // for the shapes that use all registers of the 40-register cap
+    for (uint32_t pb : {32u, 64u})
+        for (uint32_t blk : {256u, 512u})
+            for (uint32_t R : {2u, 4u, 8u}) {
+                LaunchConfig c{pb, 1, 0, blk, R, 0};
+                if (!launch_config_valid(c, L, rows)) continue;
+                const uint64_t items = rows / R * (L / pb);
+                const uint64_t full = (items + blk - 1) / blk;
+                for (uint64_t g : {full, full / 4})
+                    if (g > 0 && g <= 65535u * 16u) {
+                        c.grid = (uint32_t)g;
+                        out.push_back(c);
+                    }
+            }
     return out;
 }
 
