@@ -88,6 +88,8 @@ typedef struct {
     ising_init init;        /* initial state */
     const void *init_data;  /* host data for FROM_BUFFER (int8) / FROM_PACKED (words); else NULL */
     uint32_t word_bits;     /* 32, 64, or 0 = automatic (64 when L >= 2^16, else 32) */
+    uint64_t first_sweep;   /* sweeps already applied to the initial state (resuming a saved
+                               lattice: the next sweep uses Philox counter word 2 = first_sweep) */
 } ising_params;
 
 typedef struct {
@@ -224,7 +226,7 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
  * changes where and when sites are updated, never how.
  *
  * Options (zero = default):
- *   block          threads per CTA, 256 or 512 (512)
+ *   block          threads per CTA, 128, 256 or 512 (512)
  *   ctas_per_sm    resident CTAs per SM the plan is made for (2); each CTA gets
  *                  that share of the SM's shared memory
  *   rows_per_item  rows one thread walks per item (4)

@@ -42,7 +42,8 @@ class IsingError(RuntimeError):
 class IsingParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_uint64), ("T", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream_id", ctypes.c_uint32), ("init", ctypes.c_int),
-                ("init_data", ctypes.c_void_p), ("word_bits", ctypes.c_uint32)]
+                ("init_data", ctypes.c_void_p), ("word_bits", ctypes.c_uint32),
+                ("first_sweep", ctypes.c_uint64)]
 
 
 class IsingObs(ctypes.Structure):
@@ -490,7 +491,7 @@ class Lattice:
 
     def __init__(self, L: int, T: float, seed: int = 0, stream_id: int = 0, init: str = "hot",
                  spins: np.ndarray | None = None, packed: np.ndarray | None = None,
-                 word_bits: int = 0, stream=None):
+                 word_bits: int = 0, stream=None, first_sweep: int = 0):
         self._h = None
         data = None
         if spins is not None:
@@ -503,7 +504,7 @@ class Lattice:
         self._keep = data
         p = IsingParams(L=L, T=T, seed=seed, stream_id=stream_id, init=INIT_MODES[init],
                         init_data=data.ctypes.data if data is not None else None,
-                        word_bits=word_bits)
+                        word_bits=word_bits, first_sweep=first_sweep)
         self._h = ising_create(p, stream)
         self._keep = None
         self.L, self.T, self.seed, self.stream_id = L, T, seed, stream_id
@@ -560,6 +561,26 @@ class Lattice:
     def autotune(self, reps: int = 3) -> tuple[dict, float]:
         """Pick the fastest launch configuration (results do not depend on it)."""
         return ising_autotune(self._h, reps)
+
+    def save(self, path: str):
+        """Checkpoint: the packed lattice, its parameters, sweep count and samples
+        (a .npz file).  Lattice.load(path) resumes it bit for bit: the random
+        draws depend only on (seed, stream_id, sweep index, site)."""
+        M, E = self.samples()
+        np.savez(path, packed=self.packed(), L=self.L, T=self.T, seed=self.seed,
+                 stream_id=self.stream_id, word_bits=self.word_bits, sweeps_done=self.sweeps_done,
+                 M=M, E=E)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Lattice":
+        """Resumes a checkpoint written by save().  The samples recorded before the
+        checkpoint are returned by `restored_samples`, not counted by measure()."""
+        z = np.load(path)
+        lat = cls(int(z["L"]), float(z["T"]), seed=int(z["seed"]), stream_id=int(z["stream_id"]),
+                  packed=z["packed"], word_bits=int(z["word_bits"]), stream=stream,
+                  first_sweep=int(z["sweeps_done"]))
+        lat.restored_samples = (z["M"], z["E"])
+        return lat
 
     @property
     def sweeps_done(self) -> int:

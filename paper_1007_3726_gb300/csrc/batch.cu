@@ -167,6 +167,130 @@ __device__ __forceinline__ void batch_item(const BatchStrip &st, const HalfSweep
     }
 }
 
+// A CTA that holds one whole lattice (the lattice fits its shared memory and
+// has no neighbour strips): the step arguments stay in registers, the periodic
+// wrap is done by indexing instead of halo copies, and each step needs one
+// barrier (plus one when the step is counted).
+template <int INS, int NQ>
+__device__ __forceinline__ void whole_item(const BatchStrip &st, const HalfSweepArgs &a, uint32_t li,
+                                           uint32_t R, uint32_t p, bool count, unsigned int &cu,
+                                           unsigned int &ca)
+{
+    extern __shared__ uint64_t sm[];
+    constexpr uint32_t S = 8 / NQ;
+    const uint32_t W = st.W, nrows = st.nrows;
+    const uint32_t sub = (S == 1) ? 0u : (li & (S - 1));
+    const uint32_t rest = (S == 1) ? li : (li / S);
+    const uint32_t rb = ((W & (W - 1)) == 0) ? (rest >> (31 - __clz(W))) : rest / W;
+    const uint32_t w = rest - rb * W;
+    const uint32_t wl = (w == 0) ? W - 1 : w - 1;
+    const uint32_t wr = (w + 1 == W) ? 0 : w + 1;
+    const uint32_t r0 = rb * R, r1 = min(r0 + R, nrows);  // R is a power of two
+    uint64_t *const base = sm + st.smem_off + W;  // row 0 of the lattice
+    uint64_t *row = base + (uint64_t)r0 * W;
+    uint64_t up = base[(uint64_t)(r0 == 0 ? nrows - 1 : r0 - 1) * W + w];
+    uint64_t cur = row[w];
+    const uint64_t groups_per_row = st.L >> 3;
+    uint64_t g = (uint64_t)r0 * groups_per_row + (uint64_t)w * 8u;
+    uint32_t off = (r0 + p) & 1u;
+    for (uint32_t r = r0; r < r1; ++r) {
+        const uint64_t *dnrow = (r + 1 == nrows) ? base : row + W;
+        const uint64_t dn = dnrow[w];
+        const uint64_t nw = update_word<uint64_t, INS, NQ>(a, cur, up, dn, row[wl], row[wr], off, g, count, cu,
+                                                           ca, sub * NQ);
+        if (NQ == 8) {
+            row[w] = nw;
+        } else if (NQ == 4) {
+            reinterpret_cast<uint32_t *>(row + w)[sub] = (uint32_t)(nw >> (32 * sub));
+        } else if (NQ == 2) {
+            reinterpret_cast<uint16_t *>(row + w)[sub] = (uint16_t)(nw >> (16 * sub));
+        } else {
+            reinterpret_cast<uint8_t *>(row + w)[sub] = (uint8_t)(nw >> (8 * sub));
+        }
+        up = nw;
+        cur = dn;
+        row += W;
+        g += groups_per_row;
+        off ^= 1u;
+    }
+}
+
+template <int INS>
+__device__ void whole_lattices_steps(const BatchLaunchArgs &A, const BatchStrip *sst, const uint32_t *st0,
+                                     const uint32_t *strip_R, const uint32_t *strip_S, uint32_t *rec_phase,
+                                     uint32_t *rec_slot, unsigned int (*cnt)[2], uint32_t ns)
+{
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    if (tid < ns) {
+        cnt[tid][0] = 0u;
+        cnt[tid][1] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t s = 0; s < A.max_steps; ++s) {
+        const uint32_t p = s & 1u;
+        bool any_count = false;
+        for (uint32_t k = 0; k < ns; ++k) {
+            const BatchStrip &st = sst[k];
+            if (s >= st.nsteps) continue;
+            const uint32_t t = st0[k] + (s >> 1);
+            HalfSweepArgs a;
+            strip_step_args(a, st, t, p);
+            const bool recorded = p == 1u && st.record_every != 0u && rec_phase[k] == 0u;
+            const bool count = p == 1u && (recorded || s + 1 == st.nsteps);
+            any_count |= count;
+            const uint32_t R = strip_R[k], S = strip_S[k];
+            const uint32_t lr = 31 - __clz(R);  // R and S are powers of two
+            const uint32_t items = ((st.nrows + R - 1) >> lr) * st.W * S;
+            unsigned int cu = 0, ca = 0;
+            switch (S) {
+            case 1:
+                for (uint32_t li = tid; li < items; li += nthr) whole_item<INS, 8>(st, a, li, R, p, count, cu, ca);
+                break;
+            case 2:
+                for (uint32_t li = tid; li < items; li += nthr) whole_item<INS, 4>(st, a, li, R, p, count, cu, ca);
+                break;
+            case 4:
+                for (uint32_t li = tid; li < items; li += nthr) whole_item<INS, 2>(st, a, li, R, p, count, cu, ca);
+                break;
+            default:
+                for (uint32_t li = tid; li < items; li += nthr) whole_item<INS, 1>(st, a, li, R, p, count, cu, ca);
+                break;
+            }
+            if (count) {
+                cu = __reduce_add_sync(0xFFFFFFFFu, cu);
+                ca = __reduce_add_sync(0xFFFFFFFFu, ca);
+                if ((tid & 31u) == 0 && (cu | ca)) {
+                    atomicAdd(&cnt[k][0], cu);
+                    atomicAdd(&cnt[k][1], ca);
+                }
+            }
+        }
+        __syncthreads();
+        if (p == 1u && tid < ns) {
+            // the counters of this step to the lattice's slots (the next counted
+            // step is two steps and at least one barrier away), and the next sweep
+            const BatchStrip &st = sst[tid];
+            if (s < st.nsteps) {
+                const unsigned long long c0 = cnt[tid][0], c1 = cnt[tid][1];
+                if (st.record_every != 0u && rec_phase[tid] == 0u) {
+                    const uint32_t k = rec_slot[tid]++;
+                    atomicAdd(st.samples + 2 * k, c0);
+                    atomicAdd(st.samples + 2 * k + 1, c1);
+                }
+                if (s + 1 == st.nsteps) {
+                    atomicAdd(st.final_counts, c0);
+                    atomicAdd(st.final_counts + 1, c1);
+                }
+                cnt[tid][0] = 0u;
+                cnt[tid][1] = 0u;
+                if (st.record_every != 0u) rec_phase[tid] = (rec_phase[tid] + 1 == st.record_every) ? 0u : rec_phase[tid] + 1;
+            }
+        }
+        (void)any_count;
+    }
+    __syncthreads();
+}
+
 // Each step has four phases: wait for the neighbour strips of the previous
 // step, fill the halo rows of all strips, update all strips (one flat loop
 // over the (strip, row block, word) items of the CTA, so that small lattices
@@ -184,7 +308,9 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
     uint32_t *strip_R = item_end + MS;                                    // rows per item
     uint32_t *strip_S = strip_R + MS;                                     // threads sharing one word
     uint32_t *st0 = strip_S + MS;                                         // first sweep index
-    unsigned int (*cnt)[2] = reinterpret_cast<unsigned int (*)[2]>(st0 + MS);  // step counters
+    uint32_t *rec_phase = st0 + MS;   // (t + 1) mod record_every of the sweep in progress
+    uint32_t *rec_slot = rec_phase + MS;  // the sample slot of the next recorded sweep
+    unsigned int (*cnt)[2] = reinterpret_cast<unsigned int (*)[2]>(rec_slot + MS);  // step counters
     __shared__ uint8_t scount[kMaxStripsPerCta];       // does the strip count in this step
     const uint32_t first = A.cta_first[blockIdx.x], last = A.cta_first[blockIdx.x + 1];
     const uint32_t ns = last - first;
@@ -194,6 +320,9 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
     if (tid < ns) {
         sst[tid] = A.strips[A.cta_strips[first + tid]];
         st0[tid] = A.t0[sst[tid].lat_index];
+        const uint32_t re = sst[tid].record_every;
+        rec_phase[tid] = re ? (st0[tid] + 1) % re : 1u;
+        rec_slot[tid] = 0u;
         if (sst[tid].nstrips_lat > 1) atomicOr(&cta_multi, 1);
     }
     __syncthreads();
@@ -211,7 +340,7 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
             const BatchStrip &st = sst[k];
             // enough items for every thread when the strip is small: fewer rows
             // per item first, then fewer Philox calls per thread
-            uint32_t R = A.rows_per_item, S = 1;
+            uint32_t R = 1u << (31 - __clz(A.rows_per_item | 1u)), S = 1;  // a power of two
             while (R > 1 && (uint64_t)((st.nrows + R - 1) / R) * st.W < nthr) R >>= 1;
             while (S < 8 && (uint64_t)((st.nrows + R - 1) / R) * st.W * S < nthr) S <<= 1;
             strip_R[k] = R;
@@ -220,6 +349,10 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
     }
     __syncthreads();
 
+    if (!cta_multi) {
+        // only whole lattices in this CTA: no halos, no neighbours
+        whole_lattices_steps<INS>(A, sst, st0, strip_R, strip_S, rec_phase, rec_slot, cnt, ns);
+    } else
     for (uint32_t s = 0; s < A.max_steps; ++s) {
         const uint32_t p = s & 1u;
         // 1. neighbours of the previous step
@@ -398,7 +531,7 @@ BatchKernel batch_kernel(uint32_t insert)
 namespace {
 
 // Bytes of the per-strip tables at the start of the kernel's shared memory.
-size_t table_entry_bytes() { return sizeof(BatchStrip) + sizeof(HalfSweepArgs) + 4 * 4 + 2 * 4; }
+size_t table_entry_bytes() { return sizeof(BatchStrip) + sizeof(HalfSweepArgs) + 6 * 4 + 2 * 4; }
 size_t table_bytes(size_t max_strips) { return (max_strips * table_entry_bytes() + 15) & ~(size_t)15; }
 
 ising_status bfail(ising_batch *b, cudaError_t e, const char *what)
@@ -793,9 +926,9 @@ ising_status batch_new(int device, const ising_batch_opts *opts, ising_batch **o
     ising_batch *b = new (std::nothrow) ising_batch();
     if (!b) return fail(ISING_ERR_OOM, "host allocation failed");
     if (opts) b->opts = *opts;
-    if (b->opts.block != 0 && b->opts.block != 256 && b->opts.block != 512) {
+    if (b->opts.block != 0 && b->opts.block != 128 && b->opts.block != 256 && b->opts.block != 512) {
         delete b;
-        return fail(ISING_ERR_INVALID, "block must be 256 or 512");
+        return fail(ISING_ERR_INVALID, "block must be 128, 256 or 512");
     }
     if (b->opts.insert > 2 || b->opts.rows_per_item > 64) {
         delete b;
@@ -1011,8 +1144,8 @@ ISING_API ising_status ising_batch_tune(ising_lattice *const *hs, uint32_t n, co
     struct Cand {
         uint32_t block, ctas, rows;
     };
-    const Cand cands[] = {{256, 4, 4}, {256, 4, 8}, {256, 3, 4}, {256, 2, 4},
-                          {512, 2, 4}, {512, 2, 8}, {512, 1, 4}, {256, 8, 4}};
+    const Cand cands[] = {{256, 4, 4}, {256, 4, 8}, {256, 3, 4}, {256, 2, 4}, {512, 2, 4},
+                          {512, 2, 8}, {512, 1, 4}, {256, 8, 4}, {128, 8, 4}, {128, 16, 4}};
     double best_t = 1e300;
     bool found = false;
     cudaEvent_t t0 = nullptr, t1 = nullptr;

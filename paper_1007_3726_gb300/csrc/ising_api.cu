@@ -194,6 +194,7 @@ ising_status validate_params(const ising_params *p, uint32_t *word_bits)
         return fail(ISING_ERR_INVALID, "unknown init mode %d", (int)p->init);
     if ((p->init == ISING_FROM_BUFFER || p->init == ISING_FROM_PACKED) && !p->init_data)
         return fail(ISING_ERR_INVALID, "init_data is NULL");
+    if (p->first_sweep >= 0xFFFFFFFFull) return fail(ISING_ERR_INVALID, "first_sweep must be < 2^32 - 1");
     uint32_t wb = p->word_bits;
     if (wb == 0) wb = p->L >= 65536 ? 64 : 32;
     if (wb != 32 && wb != 64) return fail(ISING_ERR_INVALID, "word_bits must be 0, 32 or 64");
@@ -251,6 +252,7 @@ ising_status ising_create(const ising_params *params, void *cuda_stream, ising_l
     h->stream = (cudaStream_t)cuda_stream;
     h->alloc = current_allocator();
     h->key = make_round_keys(params->seed);
+    h->sweeps_done = params->first_sweep;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) {
         delete h;
