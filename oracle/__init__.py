@@ -80,6 +80,16 @@ def _load():
                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_uint32, _i64p, _i64p]
     lib.orc_cold_tiled_counts.restype = ctypes.c_int
+    lib.orc_half_sweep_field.argtypes = [_i8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                         ctypes.c_double, _i64p, _i64p]
+    lib.orc_run_field.argtypes = [_i8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
+                                  _i64p, _i64p, _i64p, _i64p, ctypes.c_int]
+    lib.orc_run_field.restype = ctypes.c_int
+    lib.orc_field_thresholds.argtypes = [ctypes.c_double, ctypes.c_double, _u32p,
+                                         ctypes.POINTER(ctypes.c_uint8)]
+    lib.orc_field_thresholds.restype = ctypes.c_int
     lib.orc_moments.argtypes = [_i64p, _i64p, ctypes.c_uint64, ctypes.c_uint64,
                                 ctypes.c_double, ctypes.c_double, _dblp]
     lib.orc_moments.restype = ctypes.c_uint64
@@ -197,6 +207,49 @@ def cold_tiled_counts(L: int, k: int, seed: int, stream_id: int, thr4: int, thr8
                                        _ptr(M, ctypes.c_int64), _ptr(E, ctypes.c_int64))
     if rc != 0:
         raise ValueError("tile_rows must divide L and leave room for the margins (%d)" % rc)
+    return M, E
+
+
+# ------------------------------------------------------------ field H != 0 ---
+def field_thresholds(T: float, H: float):
+    """(thr, always): 10 thresholds and always-accept flags indexed 5 i + c, with i = 0
+    for S = -1 and 1 for S = +1 and c the number of anti-aligned neighbours."""
+    thr = np.zeros(10, dtype=np.uint32)
+    alw = np.zeros(10, dtype=np.uint8)
+    if _load().orc_field_thresholds(float(T), float(H), _ptr(thr, ctypes.c_uint32),
+                                    _ptr(alw, ctypes.c_uint8)) != 0:
+        raise ValueError("T must be finite and positive and H finite: %r, %r" % (T, H))
+    return thr, alw.astype(bool)
+
+
+def half_sweep_field(s: np.ndarray, t: int, p: int, seed: int, stream_id: int, T: float, H: float):
+    """One checkerboard step in a field H, in place on a periodic lattice;
+    returns the incremental (dM, dE_bond)."""
+    L = s.shape[0]
+    assert s.shape == (L, L) and s.dtype == np.int8 and s.flags.c_contiguous
+    dM = ctypes.c_int64()
+    dE = ctypes.c_int64()
+    _load().orc_half_sweep_field(_ptr(s, ctypes.c_int8), L, t, p, seed, stream_id, float(T), float(H),
+                                 ctypes.byref(dM), ctypes.byref(dE))
+    return int(dM.value), int(dE.value)
+
+
+def run_field(s: np.ndarray, nsweeps: int, seed: int, stream_id: int, T: float, H: float,
+              t0: int = 0, check: bool = True, M0=None, E0=None):
+    """Sweeps t0 .. t0+nsweeps-1 in a field H, in place; returns (M, E_bond) after each."""
+    L = s.shape[0]
+    assert s.shape == (L, L) and s.dtype == np.int8 and s.flags.c_contiguous
+    if M0 is None or E0 is None:
+        M0, E0 = recount(s)
+    m = ctypes.c_int64(M0)
+    e = ctypes.c_int64(E0)
+    M = np.zeros(nsweeps, dtype=np.int64)
+    E = np.zeros(nsweeps, dtype=np.int64)
+    rc = _load().orc_run_field(_ptr(s, ctypes.c_int8), L, t0, nsweeps, seed, stream_id, float(T),
+                               float(H), ctypes.byref(m), ctypes.byref(e), _ptr(M, ctypes.c_int64),
+                               _ptr(E, ctypes.c_int64), 1 if check else 0)
+    if rc != 0:
+        raise AssertionError("incremental M/E differ from the recount after sweep %d" % (t0 + rc - 1))
     return M, E
 
 

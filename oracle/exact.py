@@ -1,11 +1,11 @@
-"""Exact references for the 2D Ising model (J = 1, H = 0, periodic boundaries).
+"""Exact references for the 2D Ising model (J = 1, periodic boundaries, field H).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-* ``enumerate_averages(L, T)`` - brute force over all 2^(L*L) states (L <= 4):
+* ``enumerate_averages(L, T, H=0)`` - brute force over all 2^(L*L) states (L <= 4):
   the plain definition of the Boltzmann averages of the Hamiltonian of Sec. 3,
-  Eq. 1.
-* ``transfer_averages(L, T)`` - the same averages by a row-to-row transfer
+  Eq. 1, weight exp(-(E - H M)/T) with E the bond energy.
+* ``transfer_averages(L, T, H=0)`` - the same averages by a row-to-row transfer
   matrix that keeps the magnetisation distribution (any L up to about 8).
 * ``onsager_tc()``, ``onsager_m0(T)``, ``onsager_u(T)`` - Onsager's exact
   critical temperature (quoted as T_C ~ 2.269185 in Sec. 1), spontaneous
@@ -13,6 +13,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 * ``flip_probabilities(s, p, thr4, thr8)`` - exact probability that each site
   flips in one checkerboard step from state ``s`` (Sec. 3 acceptance rule with
   integer thresholds).
+* ``metropolis_probabilities(s, p, T, H)`` - the same in a field, from the real
+  Metropolis factor min(1, exp(-dE/T)) with dE = 2 S (sum_n S_n + H).
 """
 from __future__ import annotations
 
@@ -39,6 +41,7 @@ def _averages_from_weights(E, M, logw, N, T):
     m = M / N
     e = E / N
     out = {
+        "mean_m": float((w * m).sum() / Z),
         "mean_e": float((w * e).sum() / Z),
         "mean_e2": float((w * e * e).sum() / Z),
         "mean_abs_m": float((w * np.abs(m)).sum() / Z),
@@ -49,11 +52,13 @@ def _averages_from_weights(E, M, logw, N, T):
     return out
 
 
-def enumerate_averages(L: int, T: float) -> dict:
-    """Exact averages of e = E/N, |m|, m^2, m^4 for an L x L periodic lattice, L <= 4."""
+def enumerate_averages(L: int, T: float, H: float = 0.0) -> dict:
+    """Exact averages of m, e = E/N (bond energy), |m|, m^2, m^4 for an L x L
+    periodic lattice in a field H, L <= 4."""
     assert L * L <= 20
     E, M = _energy_mag_all_states(L)
-    return _averages_from_weights(E.astype(np.float64), M.astype(np.float64), -E / T, L * L, T)
+    return _averages_from_weights(E.astype(np.float64), M.astype(np.float64), -(E - H * M) / T,
+                                  L * L, T)
 
 
 # -------------------------------------------------------- transfer matrix ----
@@ -106,13 +111,13 @@ def density_of_states(L: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     return E_vals, M_vals, g
 
 
-def transfer_averages(L: int, T: float) -> dict:
-    """Exact averages from the density of states g(E, M)."""
+def transfer_averages(L: int, T: float, H: float = 0.0) -> dict:
+    """Exact averages in a field H from the density of states g(E, M)."""
     E_vals, M_vals, g = density_of_states(L)
     ii, kk = np.nonzero(g)
     E = E_vals[ii].astype(np.float64)
     M = M_vals[kk].astype(np.float64)
-    logw = np.log(g[ii, kk]) - E / T
+    logw = np.log(g[ii, kk]) - (E - H * M) / T
     return _averages_from_weights(E, M, logw, L * L, T)
 
 
@@ -152,5 +157,19 @@ def flip_probabilities(s: np.ndarray, p: int, thr4: int, thr8: int) -> np.ndarra
     nsum = np.roll(s, 1, 0) + np.roll(s, -1, 0) + np.roll(s, 1, 1) + np.roll(s, -1, 1)
     dE = 2 * s * nsum
     prob = np.where(dE <= 0, 1.0, np.where(dE == 4, thr4 / 2.0 ** 32, thr8 / 2.0 ** 32))
+    y, x = np.indices((L, L))
+    return np.where(((x + y) & 1) == p, prob, 0.0)
+
+
+def metropolis_probabilities(s: np.ndarray, p: int, T: float, H: float) -> np.ndarray:
+    """Probability that each site of ``s`` flips in the checkerboard step of parity p
+    in a field H: min(1, exp(-dE/T)) with dE = 2 S (sum_n S_n + H) for the sites of
+    parity p (Sec. 3), 0 for the others.  Real numbers, not the integer thresholds:
+    they differ from thr / 2^32 by less than 2^-32."""
+    L = s.shape[0]
+    s = s.astype(np.float64)
+    nsum = np.roll(s, 1, 0) + np.roll(s, -1, 0) + np.roll(s, 1, 1) + np.roll(s, -1, 1)
+    dE = 2.0 * s * (nsum + H)
+    prob = np.where(dE <= 0, 1.0, np.exp(-np.maximum(dE, 0.0) / T))
     y, x = np.indices((L, L))
     return np.where(((x + y) & 1) == p, prob, 0.0)

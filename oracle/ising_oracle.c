@@ -11,9 +11,10 @@
  * +1 or -1) and its own energy and magnetisation bookkeeping.
  *
  * What it follows:
- *   - Hamiltonian H = -J sum_<ij> S_i S_j - H sum_i S_i with J = 1, H = 0
- *     (Sec. 3, Eq. 1), on an L x L square lattice with periodic boundaries
- *     (Sec. 6.1, Fig. 4 caption: outer borders joined periodically).
+ *   - Hamiltonian H = -J sum_<ij> S_i S_j - H sum_i S_i with J = 1 (Sec. 3,
+ *     Eq. 1), on an L x L square lattice with periodic boundaries (Sec. 6.1,
+ *     Fig. 4 caption: outer borders joined periodically).  The paper sets the
+ *     field H to zero; the *_field functions at the end keep it.
  *   - Metropolis acceptance: a move with energy change dE <= 0 is always
  *     taken, otherwise with probability exp(-dE/T) (Sec. 3); the factors for
  *     the two positive energy changes dE in {4, 8} are fixed on the host per
@@ -363,4 +364,101 @@ uint64_t orc_moments(const int64_t *M, const int64_t *E, uint64_t n, uint64_t bu
     out[7] = N * (out[2] - out[1] * out[1]) / T;
     out[8] = N * (out[5] - out[4] * out[4]) / (T * T);
     return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nonzero field (Sec. 3, Eq. 1 with H != 0).  Flipping S(x, y), whose four   */
+/* neighbours sum to n, changes the energy by dE = 2 S (n + H): the bond part */
+/* 2 S n and the field part 2 S H.  The move is taken when dE <= 0, else when */
+/* u < floor(2^32 exp(-dE/T)), the factor fixed in FP64 for this dE (the      */
+/* thresholds of Sec. 3 now depend on the spin as well as on n).  Whole       */
+/* periodic lattice; the draws follow the same site/counter contract.  dM and */
+/* dE_bond receive the changes of M and of the bond energy -sum S_i S_j (the  */
+/* field energy is -H M).                                                     */
+/* ------------------------------------------------------------------------ */
+void orc_half_sweep_field(int8_t *s, uint64_t L, uint64_t t, uint32_t p, uint64_t seed,
+                          uint32_t stream_id, double T, double H, int64_t *dM_out,
+                          int64_t *dE_out)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint32_t c3 = (stream_id << 1) | (p & 1u);
+    int64_t dM = 0, dEb = 0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : dM, dEb) schedule(static) if (L * L >= (1u << 18))
+#endif
+    for (int64_t r = 0; r < (int64_t)L; ++r) {
+        uint64_t y = (uint64_t)r;
+        uint64_t r_up = (y + L - 1) % L, r_dn = (y + 1) % L;
+        for (uint64_t x = 0; x < L; ++x) {
+            if (((x + y) & 1u) != p) continue;
+            uint64_t j = y * (L / 2) + (x >> 1);
+            uint64_t g = j >> 2;
+            uint32_t ctr[4] = {(uint32_t)g, (uint32_t)(g >> 32), (uint32_t)t, c3};
+            uint32_t draws[4];
+            orc_philox4x32_10(ctr, key, draws);
+            uint32_t u = draws[j & 3u];
+            int v = s[y * L + x];
+            int nsum = s[y * L + (x + L - 1) % L] + s[y * L + (x + 1) % L] + s[r_up * L + x] +
+                       s[r_dn * L + x];
+            double dE = 2.0 * (double)v * ((double)nsum + H);
+            int accept = dE <= 0.0 ? 1 : (u < threshold_of(dE, T));
+            if (accept) {
+                s[y * L + x] = (int8_t)(-v);
+                dM -= 2 * v;
+                dEb += 2 * v * nsum;
+            }
+        }
+    }
+    if (dM_out) *dM_out = dM;
+    if (dE_out) *dE_out = dEb;
+}
+
+/* Sweeps t0 .. t0 + nsweeps - 1 in a field, as orc_run (M, E = bond energy). */
+int orc_run_field(int8_t *s, uint64_t L, uint64_t t0, uint64_t nsweeps, uint64_t seed,
+                  uint32_t stream_id, double T, double H, int64_t *M_run, int64_t *E_run,
+                  int64_t *M, int64_t *E, int check)
+{
+    int64_t m = *M_run, e = *E_run;
+    for (uint64_t i = 0; i < nsweeps; ++i) {
+        for (uint32_t p = 0; p < 2; ++p) {
+            int64_t dM, dE;
+            orc_half_sweep_field(s, L, t0 + i, p, seed, stream_id, T, H, &dM, &dE);
+            m += dM;
+            e += dE;
+        }
+        if (check) {
+            int64_t mr, er;
+            orc_recount(s, L, &mr, &er);
+            if (mr != m || er != e) {
+                *M_run = m;
+                *E_run = e;
+                return (int)(1 + i);
+            }
+        }
+        if (M) M[i] = m;
+        if (E) E[i] = e;
+    }
+    *M_run = m;
+    *E_run = e;
+    return 0;
+}
+
+/* The acceptance of a site in a field by class: spin S (index 0 for -1, 1 for */
+/* +1) and c anti-aligned neighbours (neighbour sum n = S (4 - 2c)).  thr[5 i + c] */
+/* = floor(2^32 exp(-dE/T)) for dE = 2 S (n + H) > 0, always[5 i + c] = 1 where */
+/* dE <= 0 (thr 0 there).  Returns -1 for T not finite and positive or H not   */
+/* finite.                                                                     */
+int orc_field_thresholds(double T, double H, uint32_t thr[10], uint8_t always[10])
+{
+    if (!(T > 0.0) || !isfinite(T) || !isfinite(H)) return -1;
+    for (int i = 0; i < 2; ++i) {
+        int v = i ? 1 : -1;
+        for (int c = 0; c < 5; ++c) {
+            int nsum = v * (4 - 2 * c);
+            double dE = 2.0 * (double)v * ((double)nsum + H);
+            always[5 * i + c] = dE <= 0.0;
+            thr[5 * i + c] = dE <= 0.0 ? 0u : threshold_of(dE, T);
+        }
+    }
+    return 0;
 }
