@@ -127,10 +127,15 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- profiles --
+KERNEL_SOURCES = ("kernels.cu", "sweep_device.cuh")
+
+
 def kernel_source_hash() -> str:
+    """sha256[:16] of the half-sweep kernel's sources, concatenated in order."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1007_3726_gb300", "csrc", "kernels.cu"), "rb") as f:
-        h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1007_3726_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -142,7 +147,7 @@ def profiled_traffic():
         text = open(path).read()
     except OSError:
         return None
-    m = re.search(r"kernels\.cu`?\s+sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
+    m = re.search(r"sweep_device\.cuh`?\s+sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
     t = re.search(r"dram bytes per launch:\s*`?([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != kernel_source_hash():
         return None
@@ -220,8 +225,9 @@ def run_reference(args, ws, rank):
 # -------------------------------------------------------------------- ours --
 def extras(P, stream):
     """Other workloads, on rank 0 at N = 1: the L = 64 lattice (plain launches
-    against one persistent launch) and the 128-lattice finite-size-scaling batch
-    (one tuned persistent launch against sequential plain launches)."""
+    against one persistent launch), the 128-lattice finite-size-scaling batch
+    (one tuned persistent launch against sequential plain launches) and the
+    L = 32768 lattice in a field."""
     import numpy as np
     import torch
 
@@ -287,6 +293,18 @@ def extras(P, stream):
                 "plain: 2 launches per sweep per lattice, 200 sweeps each"}
     for lat in lats:
         lat.close()
+
+    # the same L = 32768 lattice in a field H = 0.1 (ten acceptance classes)
+    f = P.Lattice(32768, 2.269185, seed=7, init="hot", H=0.1)
+    f.sweep(10, 1)
+    f.measure()
+    t = time.perf_counter()
+    f.sweep(200, 1)
+    f.measure()
+    t_f = time.perf_counter() - t
+    out["field_L32768_H0.1"] = {"attempts_per_ns": 32768 ** 2 * 200 / t_f / 1e9,
+                                "note": "200 sweeps, M/E every sweep, wall time of one call"}
+    f.close()
     return out
 
 

@@ -90,6 +90,10 @@ typedef struct {
     uint32_t word_bits;     /* 32, 64, or 0 = automatic (64 when L >= 2^16, else 32) */
     uint64_t first_sweep;   /* sweeps already applied to the initial state (resuming a saved
                                lattice: the next sweep uses Philox counter word 2 = first_sweep) */
+    double H;               /* external field of Sec. 3, Eq. 1 (finite; 0 = the paper's case).
+                               A nonzero field runs the field kernel of ising_sweep; the
+                               recorded E stays the bond energy -sum S_i S_j (the field
+                               energy is -H M) */
 } ising_params;
 
 typedef struct {
@@ -125,6 +129,29 @@ ISING_API ising_status ising_create(const ising_params *params, void *cuda_strea
  */
 ISING_API ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_every,
                          int64_t *M_out, int64_t *E_out, uint64_t cap);
+
+/* ---- field and temperature changes ---------------------------------------- */
+
+/*
+ * In a field H (Sec. 3, Eq. 1) flipping S with c anti-aligned neighbours
+ * (neighbour sum n = S (4 - 2c)) changes the energy by dE = 2 S (n + H); the
+ * move is taken when dE <= 0, else when the site's draw u < floor(2^32
+ * exp(-dE/T)).  Writes the acceptance of the ten classes, index 5 i + c with
+ * i = 0 for S = -1 and 1 for S = +1: always[k] = 1 where dE <= 0 (thr[k] = 0
+ * there), else thr[k].  H = 0 gives thr8 at c = 0 and thr4 at c = 1.
+ * ISING_ERR_INVALID for T not finite and positive or H not finite.
+ */
+ISING_API ising_status ising_field_thresholds(double T, double H, uint32_t thr[10], uint8_t always[10]);
+/*
+ * Change the temperature / the field of a lattice from its next sweep on
+ * (annealing, field sweeps).  Sweeps already queued keep the old values.  The
+ * moments of ising_measure use the current T.  Lattices in a nonzero field run
+ * through ising_sweep only (the batch and the server reject them).
+ */
+ISING_API ising_status ising_set_temperature(ising_lattice *h, double T);
+ISING_API ising_status ising_set_field(ising_lattice *h, double H);
+/* The current T and H of a lattice (either pointer may be NULL). */
+ISING_API ising_status ising_get_params(const ising_lattice *h, double *T, double *H);
 
 /*
  * Waits for the handle's stream and fills *out: counters, the current M and E,
@@ -250,7 +277,9 @@ typedef struct {
 /* Plans a batch of n distinct handles on one device; each run advances handle
  * i by nsweeps[i] sweeps (1 .. 2^30) and records samples every record_every
  * sweeps as ising_sweep does.  ISING_ERR_INVALID if the lattices do not fit in
- * the GPU's shared memory at once.  The handles must outlive the batch. */
+ * the GPU's shared memory at once, or if one is in a nonzero field.  The batch
+ * takes each lattice's temperature when it is created.  The handles must
+ * outlive the batch. */
 ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
                                           uint32_t record_every, const ising_batch_opts *opts,
                                           ising_batch **out);

@@ -43,7 +43,7 @@ class IsingParams(ctypes.Structure):
     _fields_ = [("L", ctypes.c_uint64), ("T", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("stream_id", ctypes.c_uint32), ("init", ctypes.c_int),
                 ("init_data", ctypes.c_void_p), ("word_bits", ctypes.c_uint32),
-                ("first_sweep", ctypes.c_uint64)]
+                ("first_sweep", ctypes.c_uint64), ("H", ctypes.c_double)]
 
 
 class IsingObs(ctypes.Structure):
@@ -172,6 +172,12 @@ def load(path: str | None = None):
                               ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                               ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p],
                              ctypes.c_int),
+        "ising_field_thresholds": ([ctypes.c_double, ctypes.c_double, _u32p,
+                                    ctypes.POINTER(ctypes.c_uint8)], ctypes.c_int),
+        "ising_set_temperature": ([H, ctypes.c_double], ctypes.c_int),
+        "ising_set_field": ([H, ctypes.c_double], ctypes.c_int),
+        "ising_get_params": ([H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                             ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
@@ -210,6 +216,29 @@ def ising_thresholds(T: float) -> tuple[int, int]:
 
 
 thresholds = ising_thresholds
+
+
+def ising_field_thresholds(T: float, H: float):
+    """(thr, always) of the ten classes in a field, index 5 i + c (i = 0 for S = -1)."""
+    thr = np.zeros(10, dtype=np.uint32)
+    alw = np.zeros(10, dtype=np.uint8)
+    _check(load().ising_field_thresholds(float(T), float(H), thr.ctypes.data_as(_u32p),
+                                         alw.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return thr, alw.astype(bool)
+
+
+def ising_set_temperature(h, T: float):
+    _check(load().ising_set_temperature(h, float(T)))
+
+
+def ising_set_field(h, H: float):
+    _check(load().ising_set_field(h, float(H)))
+
+
+def ising_get_params(h) -> tuple[float, float]:
+    T, H = ctypes.c_double(), ctypes.c_double()
+    _check(load().ising_get_params(h, ctypes.byref(T), ctypes.byref(H)))
+    return T.value, H.value
 
 
 def ising_create(params: IsingParams, stream=None) -> ctypes.c_void_p:
@@ -392,9 +421,9 @@ class Server:
         _check(load().ising_server_create(ctypes.byref(o), ctypes.byref(self._s)))
 
     def submit(self, L: int, T: float, nsweeps: int, seed: int = 0, stream_id: int = 0, init: str = "hot",
-               record_every: int = 0, word_bits: int = 0, tag: int = 0) -> int:
+               record_every: int = 0, word_bits: int = 0, tag: int = 0, H: float = 0.0) -> int:
         p = IsingParams(L=L, T=T, seed=seed, stream_id=stream_id, init=INIT_MODES[init], init_data=None,
-                        word_bits=word_bits)
+                        word_bits=word_bits, H=H)
         r = IsingRequest(params=p, nsweeps=nsweeps, record_every=record_every, tag=tag)
         rid = ctypes.c_uint64()
         _check(load().ising_server_submit(self._s, ctypes.byref(r), ctypes.byref(rid)))
@@ -491,7 +520,7 @@ class Lattice:
 
     def __init__(self, L: int, T: float, seed: int = 0, stream_id: int = 0, init: str = "hot",
                  spins: np.ndarray | None = None, packed: np.ndarray | None = None,
-                 word_bits: int = 0, stream=None, first_sweep: int = 0):
+                 word_bits: int = 0, stream=None, first_sweep: int = 0, H: float = 0.0):
         self._h = None
         data = None
         if spins is not None:
@@ -504,15 +533,31 @@ class Lattice:
         self._keep = data
         p = IsingParams(L=L, T=T, seed=seed, stream_id=stream_id, init=INIT_MODES[init],
                         init_data=data.ctypes.data if data is not None else None,
-                        word_bits=word_bits, first_sweep=first_sweep)
+                        word_bits=word_bits, first_sweep=first_sweep, H=H)
         self._h = ising_create(p, stream)
         self._keep = None
-        self.L, self.T, self.seed, self.stream_id = L, T, seed, stream_id
+        self.L, self.seed, self.stream_id = L, seed, stream_id
         self.word_bits = ising_info(self._h)[0]
 
     @property
     def handle(self):
         return self._h
+
+    @property
+    def T(self) -> float:
+        return ising_get_params(self._h)[0]
+
+    @property
+    def H(self) -> float:
+        return ising_get_params(self._h)[1]
+
+    def set_temperature(self, T: float):
+        """New temperature from the next sweep on (annealing)."""
+        ising_set_temperature(self._h, T)
+
+    def set_field(self, H: float):
+        """New external field from the next sweep on (Eq. 1; 0 = the paper's case)."""
+        ising_set_field(self._h, H)
 
     def sweep(self, nsweeps: int, record_every: int = 0, collect: bool = False):
         """Run sweeps; with collect=True return this call's (M, E) samples."""
@@ -567,7 +612,7 @@ class Lattice:
         (a .npz file).  Lattice.load(path) resumes it bit for bit: the random
         draws depend only on (seed, stream_id, sweep index, site)."""
         M, E = self.samples()
-        np.savez(path, packed=self.packed(), L=self.L, T=self.T, seed=self.seed,
+        np.savez(path, packed=self.packed(), L=self.L, T=self.T, H=self.H, seed=self.seed,
                  stream_id=self.stream_id, word_bits=self.word_bits, sweeps_done=self.sweeps_done,
                  M=M, E=E)
 
@@ -578,7 +623,7 @@ class Lattice:
         z = np.load(path)
         lat = cls(int(z["L"]), float(z["T"]), seed=int(z["seed"]), stream_id=int(z["stream_id"]),
                   packed=z["packed"], word_bits=int(z["word_bits"]), stream=stream,
-                  first_sweep=int(z["sweeps_done"]))
+                  first_sweep=int(z["sweeps_done"]), H=float(z["H"]) if "H" in z else 0.0)
         lat.restored_samples = (z["M"], z["E"])
         return lat
 

@@ -1,7 +1,7 @@
 """Command-line runner: one lattice through the C ABI, observables as JSON.
 
     python -m paper_1007_3726_gb300 --L 32768 --T 2.269185 --seed 7 --init hot \
-        --sweeps 1000 --record-every 1 [--word-bits 32] [--time]
+        --sweeps 1000 --record-every 1 [--word-bits 32] [--H 0.1] [--time]
     python -m paper_1007_3726_gb300 fss-batch --sweeps 10000   (128 lattices, one launch)
 """
 import argparse
@@ -45,6 +45,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_1007_3726_gb300")
     ap.add_argument("--L", type=int, default=1024)
     ap.add_argument("--T", type=float, default=2.269185)
+    ap.add_argument("--H", type=float, default=0.0, help="external field (Eq. 1)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--stream-id", type=int, default=0)
     ap.add_argument("--init", default="hot", choices=["hot", "cold_up", "cold_down"])
@@ -60,7 +61,8 @@ def main(argv=None):
     import paper_1007_3726_gb300 as P
 
     P.load()
-    lat = P.Lattice(a.L, a.T, seed=a.seed, stream_id=a.stream_id, init=a.init, word_bits=a.word_bits)
+    lat = P.Lattice(a.L, a.T, seed=a.seed, stream_id=a.stream_id, init=a.init, word_bits=a.word_bits,
+                    H=a.H)
     if a.autotune:
         cfg, _ = lat.autotune()
     if a.launch:
@@ -71,7 +73,7 @@ def main(argv=None):
     lat.sweep(a.sweeps, a.record_every)
     d = lat.measure()
     el = time.perf_counter() - t0
-    d["L"], d["T"], d["word_bits"] = a.L, a.T, lat.word_bits
+    d["L"], d["T"], d["H"], d["word_bits"] = a.L, a.T, a.H, lat.word_bits
     d["launch"] = lat.launch
     if a.time:
         d["seconds"] = el

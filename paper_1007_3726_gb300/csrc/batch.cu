@@ -1008,6 +1008,8 @@ ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, 
         if (st != ISING_OK) return st;
         for (uint32_t k = 0; k < i; ++k)
             if (hs[k] == hs[i]) return fail(ISING_ERR_INVALID, "a handle appears twice");
+        if (hs[i]->H != 0.0)
+            return fail(ISING_ERR_INVALID, "lattice %u is in a nonzero field; it runs through ising_sweep", i);
     }
     ising_batch *b = nullptr;
     ising_status st = batch_new(hs[0]->device, opts, &b);

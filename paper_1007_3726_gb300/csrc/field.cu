@@ -1,0 +1,194 @@
+// The checkerboard step in a nonzero external field H (Sec. 3, Eq. 1 keeps the
+// term -H sum_i S_i; the paper then sets H = 0).
+//
+// Flipping S with c anti-aligned neighbours (neighbour sum n = S (4 - 2c))
+// changes the energy by dE = 2 S (n + H) = 2 (4 - 2c) + 2 S H, so the
+// acceptance depends on the class (S, c): ten classes instead of the three of
+// the zero-field update.  The host fixes, per class, either "always" (dE <= 0)
+// or the threshold floor(2^32 exp(-dE/T)) (Sec. 3: the factors are computed on
+// the CPU per temperature and passed to the kernel).
+//
+// Per word the kernel forms the four neighbour words and the bit-sliced count
+// c = b0 + 2 b1 + 4 b2 of the energy variables of Sec. 4, Eq. 4 (a full adder
+// tree instead of the "c >= 2 / c == 1 / c == 0" split), then
+//   always = S & [c >= k+] | ~S & [c >= k-]        (bit-parallel)
+//   P      = bits of the sites whose draw u < thr[S, c]   (per site, a table
+//            lookup in shared memory indexed by the site's 4-bit class)
+//   flip   = target mask & (always | P).
+// The draws are the same Philox4x32-10 words as in the zero-field update (the
+// counter contract does not depend on H), so H = 0 reproduces it bit for bit.
+// Lattices are processed 32 bits at a time whatever their storage width (a
+// 64-bit word is two consecutive 32-bit words).
+#include "field.h"
+#include "sweep_device.cuh"
+
+namespace ising {
+
+namespace {
+
+constexpr uint32_t kEven = 0x55555555u;
+
+// Sites with c >= k, for a uniform k in 0..5 (c = b0 + 2 b1 + 4 b2 <= 4).
+__device__ __forceinline__ uint32_t count_at_least(uint32_t k, uint32_t b0, uint32_t b1, uint32_t b2)
+{
+    return k == 0 ? ~0u : k == 1 ? (b0 | b1 | b2) : k == 2 ? (b1 | b2) : k == 3 ? ((b0 & b1) | b2)
+           : k == 4 ? b2 : 0u;
+}
+
+// One 32-bit word of target sites (see update_word for the arguments); tab is
+// the 16-entry threshold table in shared memory, index 8 S + c.
+__device__ __forceinline__ uint32_t update_word_field(const HalfSweepArgs &a, const uint32_t *tab,
+                                                      uint32_t k_up, uint32_t k_dn, uint32_t cur,
+                                                      uint32_t up, uint32_t dn, uint32_t lw, uint32_t rw,
+                                                      uint32_t off, uint64_t g, bool count,
+                                                      unsigned int &cnt_up, unsigned int &cnt_anti)
+{
+    const uint32_t left = (cur << 1) | (lw >> 31);   // bit b holds s(x - 1)
+    const uint32_t right = (cur >> 1) | (rw << 31);  // bit b holds s(x + 1)
+    const uint32_t mask = off ? (kEven << 1) : kEven;
+
+    // energy variables and the three bits of their sum c
+    const uint32_t i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
+    const uint32_t s12 = i1 ^ i2, c12 = i1 & i2;
+    const uint32_t s34 = i3 ^ i4, c34 = i3 & i4;
+    const uint32_t b0 = s12 ^ s34;
+    const uint32_t b1 = c12 ^ c34 ^ (s12 & s34);
+    const uint32_t b2 = c12 & c34;  // c == 4 (then s12 = s34 = 0)
+    const uint32_t always = (cur & count_at_least(k_up, b0, b1, b2)) |
+                            (~cur & count_at_least(k_dn, b0, b1, b2));
+
+    // the class of target site j (bit off + 2j) as two 2-bit fields at bit 2j:
+    // X = (b1 b0), Y = (S b2); its table index is X_j | Y_j << 2
+    const uint32_t X = ((b0 >> off) & kEven) | (((b1 >> off) & kEven) << 1);
+    const uint32_t Y = ((b2 >> off) & kEven) | (((cur >> off) & kEven) << 1);
+
+    const WordDraws d = word_draws_begin(a, g);
+    uint32_t P = a.zero;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t u[4];
+        word_draw_call(a, d, (uint32_t)q, u);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int pos = 8 * q + 2 * l;
+            const uint32_t idx = ((X >> pos) & 3u) | (((Y >> pos) & 3u) << 2);
+            const uint32_t thr = tab[idx];
+            const uint32_t bit = 1u << pos;
+            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+                : "+r"(P)
+                : "r"(u[l]), "r"(thr), "r"(bit));
+        }
+    }
+    const uint32_t flip = mask & (always | (P << off));
+    const uint32_t nw = cur ^ flip;
+    if (count) {
+        cnt_up += __popc(nw);
+        cnt_anti += __popc(mask & (nw ^ up)) + __popc(mask & (nw ^ dn)) + __popc(mask & (nw ^ left)) +
+                    __popc(mask & (nw ^ right));
+    }
+    return nw;
+}
+
+// Work item = (block of R rows, word column); the thread walks down its column
+// as in the zero-field kernel.  Whole periodic lattice.
+__global__ void __launch_bounds__(256) k_half_sweep_field(const __grid_constant__ HalfSweepArgs a,
+                                                          const __grid_constant__ FieldTable ft)
+{
+    __shared__ uint32_t tab[16];
+    if (threadIdx.x < 16) tab[threadIdx.x] = ft.thr[threadIdx.x];
+    __syncthreads();
+
+    uint32_t *const S = static_cast<uint32_t *>(a.spins);
+    const uint64_t rows = a.rows;
+    const uint32_t W = a.words_per_row;
+    const uint32_t R = a.rows_per_item;
+    const uint32_t nrb = (uint32_t)(rows / R);
+    const uint64_t groups_per_row = a.L >> 3;
+
+    unsigned int cnt_up = 0, cnt_anti = 0;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t rb = tid / W;
+    uint32_t w = tid - rb * W;
+    while (rb < nrb) {
+        const int64_t dl = (w == 0) ? (int64_t)W - 1 : -1;
+        const int64_t dr = (w + 1 == W) ? 1 - (int64_t)W : 1;
+        const uint64_t y0 = (uint64_t)rb * R;
+        uint32_t *p = S + y0 * W + w;
+        uint32_t up = *((y0 == 0) ? S + (rows - 1) * W + w : p - W);
+        uint32_t cur = *p;
+        uint64_t g = y0 * groups_per_row + (uint64_t)w * 4;
+        uint32_t off = (uint32_t)((y0 + a.p) & 1u);
+        for (uint32_t r = 0; r < R; ++r) {
+            uint32_t *const pn = (y0 + r + 1 == rows) ? S + w : p + W;
+            const uint32_t dn = *pn;
+            const uint32_t nw = update_word_field(a, tab, ft.k_up, ft.k_dn, cur, up, dn, p[dl], p[dr], off, g,
+                                                  a.acc != nullptr, cnt_up, cnt_anti);
+            *p = nw;
+            up = nw;
+            cur = dn;
+            p = pn;
+            g += groups_per_row;
+            off ^= 1u;
+        }
+        rb += a.stride_rb;
+        w += a.stride_w;
+        if (w >= W) {
+            w -= W;
+            ++rb;
+        }
+    }
+    if (a.acc) block_accumulate(cnt_up, cnt_anti, a.acc);
+}
+
+constexpr int kFieldBlock = 256;
+
+}  // namespace
+
+// dE = 2 S (n + H) with n = S (4 - 2c), in FP64, as the class table.
+FieldTable make_field_table(double T, double H)
+{
+    FieldTable f{};
+    f.k_up = 5;
+    f.k_dn = 5;
+    for (int i = 0; i < 2; ++i) {
+        const int v = i ? 1 : -1;
+        for (int c = 4; c >= 0; --c) {
+            const int nsum = v * (4 - 2 * c);
+            const double dE = 2.0 * (double)v * ((double)nsum + H);
+            if (dE <= 0.0) {
+                // dE falls as c grows, so the always-accepted classes are c >= k
+                (i ? f.k_up : f.k_dn) = (uint32_t)c;
+                f.thr[8 * i + c] = 0u;
+            } else {
+                f.thr[8 * i + c] = threshold_for(dE, T);
+            }
+        }
+    }
+    return f;
+}
+
+cudaError_t launch_half_sweep_field(HalfSweepArgs a, const FieldTable &ft, cudaStream_t s)
+{
+    a.rows = a.L;
+    a.first_row = 0;
+    a.update_rows = a.L;
+    a.y_offset = 0;
+    a.words_per_row = (uint32_t)(a.L / 32);
+    a.rows_per_item = 8;  // L is a multiple of 64
+    a.zero = 0u;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_half_sweep_field, kFieldBlock, 0);
+    if (per_sm <= 0) per_sm = 1;
+    if (sms <= 0) sms = 1;
+    const uint64_t items = (a.L / 8) * (uint64_t)a.words_per_row;
+    const uint64_t need = (items + kFieldBlock - 1) / kFieldBlock;
+    const uint64_t cap = (uint64_t)sms * (uint64_t)per_sm;
+    const int grid = (int)(need < cap ? need : cap);
+    prepare_half_sweep(a, grid, kFieldBlock);
+    k_half_sweep_field<<<grid, kFieldBlock, 0, s>>>(a, ft);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

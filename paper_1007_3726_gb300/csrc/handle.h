@@ -2,6 +2,7 @@
 #pragma once
 
 #include "ising.h"
+#include "field.h"
 #include "kernels.h"
 #include "runtime.h"
 
@@ -16,6 +17,8 @@ struct ising_lattice {
     uint32_t word_bits = 32;
     uint32_t W = 0;  // words per row
     uint32_t thr4 = 0, thr8 = 0;
+    double H = 0;                // external field; nonzero runs the field kernel
+    ising::FieldTable field{};   // its class thresholds at (T, H)
     size_t bytes = 0;
     int device = 0;
     cudaStream_t stream = nullptr;

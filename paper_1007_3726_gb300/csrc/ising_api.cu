@@ -189,6 +189,7 @@ ising_status validate_params(const ising_params *p, uint32_t *word_bits)
         return fail(ISING_ERR_INVALID, "L must be a multiple of 64 in [64, 2^20], got %llu",
                     (unsigned long long)p->L);
     if (!valid_temperature(p->T)) return fail(ISING_ERR_INVALID, "T must be finite and > 0");
+    if (!std::isfinite(p->H)) return fail(ISING_ERR_INVALID, "H must be finite");
     if (p->stream_id >= (1u << 31)) return fail(ISING_ERR_INVALID, "stream_id must be < 2^31");
     if (p->init < ISING_COLD_UP || p->init > ISING_FROM_PACKED)
         return fail(ISING_ERR_INVALID, "unknown init mode %d", (int)p->init);
@@ -215,6 +216,53 @@ ising_status ising_thresholds(double T, uint32_t *thr4, uint32_t *thr8)
     if (!valid_temperature(T)) return fail(ISING_ERR_INVALID, "T must be finite and > 0");
     *thr4 = threshold_for(4.0, T);
     *thr8 = threshold_for(8.0, T);
+    return ISING_OK;
+}
+
+ising_status ising_field_thresholds(double T, double H, uint32_t thr[10], uint8_t always[10])
+{
+    if (!thr || !always) return fail(ISING_ERR_INVALID, "null output");
+    if (!valid_temperature(T)) return fail(ISING_ERR_INVALID, "T must be finite and > 0");
+    if (!std::isfinite(H)) return fail(ISING_ERR_INVALID, "H must be finite");
+    const FieldTable f = make_field_table(T, H);
+    for (int i = 0; i < 2; ++i)
+        for (int c = 0; c < 5; ++c) {
+            thr[5 * i + c] = f.thr[8 * i + c];
+            always[5 * i + c] = (uint32_t)c >= (i ? f.k_up : f.k_dn);
+        }
+    return ISING_OK;
+}
+
+ising_status ising_set_temperature(ising_lattice *h, double T)
+{
+    clear_error();
+    if (!h) return fail(ISING_ERR_INVALID, "null handle");
+    if (h->failed) return fail(ISING_ERR_STATE, "handle failed earlier; destroy it");
+    if (!valid_temperature(T)) return fail(ISING_ERR_INVALID, "T must be finite and > 0");
+    h->T = T;
+    h->thr4 = threshold_for(4.0, T);
+    h->thr8 = threshold_for(8.0, T);
+    h->field = make_field_table(T, h->H);
+    return ISING_OK;
+}
+
+ising_status ising_set_field(ising_lattice *h, double H)
+{
+    clear_error();
+    if (!h) return fail(ISING_ERR_INVALID, "null handle");
+    if (h->failed) return fail(ISING_ERR_STATE, "handle failed earlier; destroy it");
+    if (!std::isfinite(H)) return fail(ISING_ERR_INVALID, "H must be finite");
+    h->H = H;
+    h->field = make_field_table(h->T, H);
+    return ISING_OK;
+}
+
+ising_status ising_get_params(const ising_lattice *h, double *T, double *H)
+{
+    clear_error();
+    if (!h) return fail(ISING_ERR_INVALID, "null handle");
+    if (T) *T = h->T;
+    if (H) *H = h->H;
     return ISING_OK;
 }
 
@@ -248,6 +296,8 @@ ising_status ising_create(const ising_params *params, void *cuda_stream, ising_l
     h->W = (uint32_t)(params->L / wb);
     h->thr4 = threshold_for(4.0, params->T);
     h->thr8 = threshold_for(8.0, params->T);
+    h->H = params->H;
+    h->field = make_field_table(params->T, params->H);
     h->bytes = (size_t)(params->L * params->L / 8);
     h->stream = (cudaStream_t)cuda_stream;
     h->alloc = current_allocator();
@@ -373,7 +423,10 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
                 else if (i + 1 == nsweeps)
                     a.acc = h->d_acc + 2 * nrec;  // state after the call
             }
-            CK(h, launch_half_sweep(a, h->launch, h->stream));
+            if (h->H != 0.0)
+                CK(h, launch_half_sweep_field(a, h->field, h->stream));
+            else
+                CK(h, launch_half_sweep(a, h->launch, h->stream));
         }
     }
     if (slot == nrec && nrec > 0 && record_every && (t0 + nsweeps) % record_every == 0) {

@@ -91,26 +91,62 @@ __device__ __forceinline__ void block_accumulate(unsigned int a, unsigned int b,
     }
 }
 
+// The Philox4x32-10 calls of one word whose first Philox group is g0, with
+// the step-uniform parts hoisted: round 1 and the word-0/word-3 half of round 2
+// come from the step-uniform values; the round-1 products A * (g0 + q) are one
+// widening multiply per word plus 64-bit additions of the constants A * q (the
+// low counter words g0 .. g0 + NB - 1 of a word never wrap, since g0 is a
+// multiple of NB).
+struct WordDraws {
+    uint64_t pa0;           // A * lo(g0)
+    uint32_t r2x2k, r2x3;   // round-2 words 2 (before the XOR) and 3 for hi(g0)
+};
+
+__device__ __forceinline__ WordDraws word_draws_begin(const HalfSweepArgs &a, uint64_t g0)
+{
+    WordDraws d;
+    const uint32_t c1 = (uint32_t)(g0 >> 32);  // the same for all groups of a word
+    d.r2x2k = a.r2x2k;
+    d.r2x3 = a.r2x3;
+    if (c1 != 0u) {
+        const uint64_t pa = (uint64_t)(a.r1x0 ^ c1) * kPhiloxMulA;
+        d.r2x2k = (uint32_t)(pa >> 32) ^ a.key.k1[1];
+        d.r2x3 = (uint32_t)pa;
+    }
+    d.pa0 = (uint64_t)(uint32_t)g0 * kPhiloxMulA;
+    return d;
+}
+
+// The four draws of call q of the word (counter low word g0 + q).
+__device__ __forceinline__ void word_draw_call(const HalfSweepArgs &a, const WordDraws &d, uint32_t q,
+                                               uint32_t (&u)[4])
+{
+    // round 1: words 0, 1 are uniform (r1x0 ^ c1, lo(B t))
+    const uint64_t pa = d.pa0 + (uint64_t)kPhiloxMulA * (uint64_t)q;
+    const uint32_t x2 = (uint32_t)(pa >> 32) ^ a.r1x2k;
+    const uint32_t x3 = (uint32_t)pa;
+    // round 2: the product A * word 0 is uniform per word
+    const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
+    uint32_t y0 = (uint32_t)(pb >> 32) ^ a.r2x0k;
+    uint32_t y1 = (uint32_t)pb;
+    uint32_t y2 = x3 ^ d.r2x2k;
+    uint32_t y3 = d.r2x3;
+    philox_rounds_from<2>(y0, y1, y2, y3, a.key);
+    u[0] = y0;
+    u[1] = y1;
+    u[2] = y2;
+    u[3] = y3;
+}
+
 // The acceptance masks of one word whose first Philox group is g0: bit
 // 8q + 2l of half (q / 4) is set when draw l of the word's call q is below the
-// threshold.  Round 1 and the word-0/word-3 half of round 2 come from the
-// step-uniform values; the round-1 products A * (g0 + q) are one widening
-// multiply per word plus 64-bit additions of the constants A * q (the low
-// counter words g0 .. g0 + NB - 1 of a word never wrap, since g0 is a
-// multiple of NB).
+// threshold.
 template <int NB, int INS, int NQ = NB>
 __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t g0,
                                                 uint32_t (&p4)[(NB + 3) / 4],
                                                 uint32_t (&p8)[(NB + 3) / 4], uint32_t q0 = 0)
 {
-    const uint32_t c1 = (uint32_t)(g0 >> 32);  // the same for all groups of a word
-    uint32_t r2x2k = a.r2x2k, r2x3 = a.r2x3;
-    if (c1 != 0u) {
-        const uint64_t pa = (uint64_t)(a.r1x0 ^ c1) * kPhiloxMulA;
-        r2x2k = (uint32_t)(pa >> 32) ^ a.key.k1[1];
-        r2x3 = (uint32_t)pa;
-    }
-    const uint64_t pa0 = (uint64_t)(uint32_t)g0 * kPhiloxMulA;
+    const WordDraws d = word_draws_begin(a, g0);
     // INS >= 1 (>= 2) starts the P4 (P8) mask from a zero the compiler cannot
     // see, so that its bit insertions stay ORs on the ALU pipe instead of
     // becoming additions on the pipe that also carries the Philox multiplies.
@@ -126,18 +162,8 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
 #pragma unroll
     for (int qq = 0; qq < NQ; ++qq) {
         const uint32_t q = (NQ == NB) ? (uint32_t)qq : q0 + (uint32_t)qq;
-        // round 1: words 0, 1 are uniform (r1x0 ^ c1, lo(B t))
-        const uint64_t pa = pa0 + (uint64_t)kPhiloxMulA * (uint64_t)q;
-        const uint32_t x2 = (uint32_t)(pa >> 32) ^ a.r1x2k;
-        const uint32_t x3 = (uint32_t)pa;
-        // round 2: the product A * word 0 is uniform per word
-        const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
-        uint32_t y0 = (uint32_t)(pb >> 32) ^ a.r2x0k;
-        uint32_t y1 = (uint32_t)pb;
-        uint32_t y2 = x3 ^ r2x2k;
-        uint32_t y3 = r2x3;
-        philox_rounds_from<2>(y0, y1, y2, y3, a.key);
-        const uint32_t u[4] = {y0, y1, y2, y3};
+        uint32_t u[4];
+        word_draw_call(a, d, q, u);
         const int h = (NQ == NB) ? (qq >> 2) : 0;
 #pragma unroll
         for (int l = 0; l < 4; ++l) {

@@ -79,6 +79,7 @@ def test_library_rejects_bad_temperature(ising, bad):
 
 @pytest.mark.parametrize("field,value", [("L", 0), ("L", 32), ("L", 100), ("L", 2 ** 21),
                                          ("T", -1.0), ("T", float("nan")),
+                                         ("H", float("nan")), ("H", float("-inf")),
                                          ("stream_id", 2 ** 31), ("word_bits", 16),
                                          ("init", 9), ("init", 3)])
 def test_create_validates_before_touching_the_gpu(ising, field, value):
@@ -91,12 +92,35 @@ def test_create_validates_before_touching_the_gpu(ising, field, value):
     assert ising.ising_last_error() != ""
 
 
+def test_library_field_thresholds_equal_oracle(ising, orc):
+    """The ten class thresholds of the field update (Eq. 1 with H != 0) are the
+    oracle's, and H = 0 reduces them to (thr8, thr4) at c = 0, 1."""
+    rng = np.random.default_rng(2)
+    cases = [(T, H) for T in (0.01, 0.7, 2.0, 2.269185, 3.5, 1e300)
+             for H in (0.0, 1e-300, 0.1, -0.1, 1.0, 2.0, -2.0, 4.0, 5.5, -1e3)]
+    cases += list(zip(rng.uniform(0.2, 20.0, 300), rng.uniform(-6.0, 6.0, 300)))
+    for T, H in cases:
+        thr, alw = ising.ising_field_thresholds(float(T), float(H))
+        othr, oalw = orc.field_thresholds(float(T), float(H))
+        assert np.array_equal(thr, othr) and np.array_equal(alw, oalw), (T, H)
+    thr4, thr8 = ising.ising_thresholds(2.269185)
+    thr, alw = ising.ising_field_thresholds(2.269185, 0.0)
+    assert list(thr) == [thr8, thr4, 0, 0, 0] * 2
+    assert list(alw) == [False, False, True, True, True] * 2
+    for bad in ((0.0, 0.0), (1.0, float("nan")), (float("inf"), 0.0)):
+        with pytest.raises(ising.IsingError):
+            ising.ising_field_thresholds(*bad)
+
+
 def test_null_handles_and_arguments(ising):
     lib = ising.load()
     assert lib.ising_destroy(None) == ising.OK
     assert lib.ising_sweep(None, 1, 0, None, None, 0) == ising.ERR_INVALID
     assert lib.ising_measure(None, None) == ising.ERR_INVALID
     assert lib.ising_create(None, None, None) == ising.ERR_INVALID
+    assert lib.ising_set_temperature(None, 2.0) == ising.ERR_INVALID
+    assert lib.ising_set_field(None, 0.5) == ising.ERR_INVALID
+    assert lib.ising_get_params(None, None, None) == ising.ERR_INVALID
     a = ising.ALLOC_FN(lambda n, s, c: None)
     assert lib.ising_set_allocator(a, ctypes.cast(None, ising.FREE_FN), None) == ising.ERR_INVALID
 
