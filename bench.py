@@ -235,13 +235,20 @@ def extras(P, stream):
 
     out = {}
     w = WL.plain_L64()
-    a = P.Lattice(**WL.lattice_kwargs(w))
-    a.sweep(20, 1)
-    a.measure()
-    t = time.perf_counter()
-    a.sweep(w["sweeps"], 1)
-    a.measure()
-    t_plain = time.perf_counter() - t
+
+    def timed_call(lat):
+        lat.sweep(20, 1)
+        lat.measure()
+        t = time.perf_counter()
+        lat.sweep(w["sweeps"], 1)
+        lat.measure()
+        return time.perf_counter() - t
+
+    a = P.Lattice(**WL.lattice_kwargs(w))            # default: the one-CTA kernel
+    t_cta = timed_call(a)
+    s = P.Lattice(**WL.lattice_kwargs(w))
+    s.set_launch(proc_bits=32, regcap=0, insert=0, block=128, rows_per_item=4, grid=0)
+    t_steps = timed_call(s)
     b_lat = P.Lattice(**WL.lattice_kwargs(w))
     with P.Batch([b_lat], [w["sweeps"]], 1) as b:
         b.run(1)
@@ -249,9 +256,16 @@ def extras(P, stream):
         b.run(1)
         t_batch = time.perf_counter() - t
     n64 = 64 * 64 * w["sweeps"]
-    out["L64_1000_sweeps"] = {"plain_attempts_per_ns": n64 / t_plain / 1e9,
-                              "persistent_attempts_per_ns": n64 / t_batch / 1e9,
-                              "note": "wall time of one call, M/E every sweep"}
+    out["L64_1000_sweeps"] = {"one_cta_attempts_per_ns": n64 / t_cta / 1e9,
+                              "step_launches_attempts_per_ns": n64 / t_steps / 1e9,
+                              "batch_attempts_per_ns": n64 / t_batch / 1e9,
+                              "one_sm_bound_attempts_per_ns": 40.27e12 / 152 / 16 / 1e9,
+                              "launch": a.launch,
+                              "note": "wall time of one call (launch, 1000 sweeps, read-back of 1000 "
+                                      "M/E samples); one CTA: ising_sweep's default at this size; step "
+                                      "launches: 2 kernels per sweep; batch: the persistent batch kernel"}
+    for x in (a, s, b_lat):
+        x.close()
 
     specs = WL.fss_batch()
     lats = [P.Lattice(**WL.lattice_kwargs(sp)) for sp in specs]

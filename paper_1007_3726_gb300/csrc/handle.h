@@ -54,4 +54,8 @@ ising_status cuda_fail(ising_lattice *h, cudaError_t e, const char *what);
 ising_status check_live(ising_lattice *h);     // not failed; its device made current
 ising_status harvest(ising_lattice *h);        // read back the last queued call's samples
 ising_status ensure_acc(ising_lattice *h, size_t slots);
+// The end of ising_sweep once its kernels are queued: the counters' read-back
+// and the sweep count; with M_out, the call's samples.
+ising_status finish_sweep_call(ising_lattice *h, uint64_t t0, uint64_t nsweeps, uint64_t nrec, int64_t *M_out,
+                               int64_t *E_out);
 }  // namespace ising

@@ -401,6 +401,23 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
     if ((st = ensure_acc(h, nrec + 1)) != ISING_OK) return st;
 
     CK(h, cudaMemsetAsync(h->d_acc, 0, (nrec + 1) * 16, h->stream));
+    if (h->launch.proc_bits == kTinyProcBits && h->H == 0.0) {
+        // the whole call in one launch of one CTA
+        TinyRunArgs ta{};
+        ta.spins = h->d_spins;
+        ta.L = h->L;
+        ta.key = h->key;
+        ta.thr4 = h->thr4;
+        ta.thr8 = h->thr8;
+        ta.c3base = h->stream_id << 1;
+        ta.t0 = (uint32_t)t0;
+        ta.nsweeps = (uint32_t)nsweeps;
+        ta.record_every = record_every;
+        ta.nrec = (uint32_t)nrec;
+        ta.acc = h->d_acc;
+        CK(h, launch_tiny(ta, h->launch.block, h->stream));
+        return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
+    }
     HalfSweepArgs a{};
     a.spins = h->d_spins;
     a.L = h->L;
@@ -434,6 +451,19 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
         CK(h, cudaMemcpyAsync(h->d_acc + 2 * nrec, h->d_acc + 2 * (nrec - 1), 16,
                               cudaMemcpyDeviceToDevice, h->stream));
     }
+    return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
+}
+
+}  // extern "C"
+
+namespace ising {
+
+// Queues the read-back of a call's counters; with M_out, waits and copies the
+// call's samples out.
+ising_status finish_sweep_call(ising_lattice *h, uint64_t t0, uint64_t nsweeps, uint64_t nrec, int64_t *M_out,
+                               int64_t *E_out)
+{
+    ising_status st;
     CK(h, cudaMemcpyAsync(h->h_acc, h->d_acc, (nrec + 1) * 16, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaEventRecord(h->ev, h->stream));
     h->sweeps_done = t0 + nsweeps;
@@ -449,6 +479,10 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
     }
     return ISING_OK;
 }
+
+}  // namespace ising
+
+extern "C" {
 
 ising_status ising_measure_from(ising_lattice *h, uint64_t first_sample, ising_obs *out)
 {

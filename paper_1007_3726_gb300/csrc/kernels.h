@@ -53,9 +53,12 @@ struct HalfSweepArgs {
 void prepare_half_sweep(HalfSweepArgs &a, int grid, int block);
 
 // A launch configuration of the half-sweep.  Every valid configuration gives
-// bit-identical results; they differ only in speed.
+// bit-identical results; they differ only in speed.  proc_bits == 8 selects the
+// one-CTA kernel of tiny.cu instead (whole lattice in shared memory, every
+// sweep of a call in one launch; only block is used, the other fields are 0,
+// 0, 1, 1).
 struct LaunchConfig {
-    uint32_t proc_bits;      // 32 or 64: bits one thread updates per row
+    uint32_t proc_bits;      // 32 or 64: bits one thread updates per row; 8: one CTA
     uint32_t regcap;         // 0: compiler's choice, 1: <= 40 registers, 2: <= 32 registers
     uint32_t insert;         // acceptance-bit insertion kept on the ALU pipe: 0 none, 1 P4, 2 P4+P8
     uint32_t block;          // 128, 256 or 512 threads
@@ -64,6 +67,31 @@ struct LaunchConfig {
 };
 
 bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows);
+
+constexpr uint32_t kTinyProcBits = 8;
+// Lattices the one-CTA kernel takes: L a power of two, 64 <= L <= 1024.
+bool tiny_lattice_ok(uint64_t L);
+// c itself if it is a configuration of the half-sweep kernel, else the fixed
+// default one (for callers that launch single steps).
+LaunchConfig plain_launch(const LaunchConfig &c);
+
+// Every sweep of one call on a whole lattice, in one launch of one CTA that
+// holds the lattice in shared memory (tiny.cu).  Samples as in ising_sweep:
+// acc[2k], acc[2k + 1] = (+1 spins, anti-aligned bonds) after the k-th recorded
+// sweep, acc[2 nrec], acc[2 nrec + 1] after the last sweep.
+struct TinyRunArgs {
+    void *spins;              // L x L/8 bytes, packed rows (any storage word width)
+    uint64_t L;
+    RoundKeys key;
+    uint32_t thr4, thr8;
+    uint32_t c3base;          // stream_id << 1
+    uint32_t t0;              // sweep index of the first sweep
+    uint32_t nsweeps;         // >= 1
+    uint32_t record_every;    // 0: record nothing
+    uint32_t nrec;            // recorded sweeps of the call
+    unsigned long long *acc;  // nrec + 1 slots of two counters
+};
+cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, cudaStream_t s);
 // Resident blocks per SM of the configuration's kernel.
 int half_sweep_blocks_per_sm(const LaunchConfig &c);
 // Grid that makes every block resident (grid == 0 resolved).

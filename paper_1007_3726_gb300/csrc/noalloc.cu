@@ -99,7 +99,7 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
     a.thr8 = threshold_for(8.0, T);
     int dev = 0;
     cudaGetDevice(&dev);
-    const LaunchConfig cfg = default_launch(dev, L, word_bits);
+    const LaunchConfig cfg = plain_launch(default_launch(dev, L, word_bits));
     uint64_t slot = 0;
     for (uint64_t i = 0; i < nsweeps && e == cudaSuccess; ++i) {
         const uint64_t t = t0 + i;

@@ -85,7 +85,7 @@ ISING_API ising_status ising_strip_step(void *d_rows, uint64_t L, uint32_t word_
     a.acc = (p == 1) ? d_counts : nullptr;
     int dev = 0;
     cudaGetDevice(&dev);
-    LaunchConfig cfg = default_launch(dev, L, word_bits);
+    LaunchConfig cfg = plain_launch(default_launch(dev, L, word_bits));
     while (cfg.rows_per_item > 1 && nrows % cfg.rows_per_item != 0) cfg.rows_per_item >>= 1;
     const cudaError_t e = launch_half_sweep(a, cfg, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return fail(ISING_ERR_CUDA, "strip step: %s", cudaGetErrorString(e));

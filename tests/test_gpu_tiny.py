@@ -1,0 +1,110 @@
+"""GPU parity of the one-CTA kernel (the whole lattice in shared memory, every
+sweep of a call in one launch; launch configurations with proc_bits == 8),
+against the oracle, bit for bit.
+
+It is the default for L <= 256, so the other parity tests at those sizes run
+through it too; here every block size and every size it takes (64 .. 1024, up
+to 128 KiB of shared memory and 256 bytes per thread) is checked, with samples
+recorded every sweep, every third sweep across split calls, and not at all.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TC = 2.269185
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1007_3726_gb300 as P
+
+    P.build()
+    P.load()
+    return P
+
+
+TINY = {"proc_bits": 8, "regcap": 0, "insert": 0, "rows_per_item": 1, "grid": 1}
+
+
+@pytest.mark.parametrize("L", [64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("block", [128, 256, 512])
+def test_tiny_sizes_and_blocks_bit_exact(P, orc, L, block):
+    n = 12 if L <= 256 else 4
+    T, seed, sid = TC, L + block, 1
+    lat = P.Lattice(L, T, seed=seed, stream_id=sid, init="hot", word_bits=64 if L >= 512 else 32)
+    lat.set_launch(**TINY, block=block)
+    assert lat.launch["proc_bits"] == 8
+    M, E = lat.sweep(n, 1, collect=True)
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_hot(L, seed, sid)
+    Mo, Eo = orc.run(s, n, seed, sid, thr4, thr8)
+    assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
+    assert np.array_equal(lat.spins(), s)
+    assert lat.recount() == orc.recount(s)
+    lat.close()
+
+
+@pytest.mark.parametrize("T", [0.8, 2.0, 3.5])
+def test_tiny_split_calls_sparse_records_and_final_state(P, orc, T):
+    """record_every = 3 over calls of 7, 13, 1, 39 and 2 sweeps (the sample phase
+    crosses call boundaries); calls with no sample still update M and E."""
+    L, seed = 128, 41
+    lat = P.Lattice(L, T, seed=seed, init="cold_up")
+    lat.set_launch(**TINY, block=256)
+    Ms, Es = [], []
+    for n in (7, 13, 1, 39, 2):
+        M, E = lat.sweep(n, 3, collect=True)
+        Ms.append(M)
+        Es.append(E)
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_cold(L, 1)
+    Mo, Eo = orc.run(s, 62, seed, 0, thr4, thr8)
+    assert np.array_equal(np.concatenate(Ms), Mo[2::3]) and np.array_equal(np.concatenate(Es), Eo[2::3])
+    d = lat.measure()
+    assert (d["M"], d["E"]) == (int(Mo[-1]), int(Eo[-1]))
+    lat.sweep(5, 0)  # nothing recorded, the final state is still counted
+    Mo2, Eo2 = orc.run(s, 5, seed, 0, thr4, thr8, t0=62)
+    d = lat.measure()
+    assert (d["M"], d["E"]) == (int(Mo2[-1]), int(Eo2[-1]))
+    assert np.array_equal(lat.spins(), s)
+
+
+def test_tiny_equals_plain_launches_on_the_L64_workload(P):
+    """L = 64, cold start, 1000 sweeps, M/E every sweep: one launch of the one-CTA
+    kernel and 2000 launches of the step kernel give the same lattice and samples."""
+    a = P.Lattice(64, TC, seed=1, init="cold_up")
+    assert a.launch["proc_bits"] == 8  # the default at this size
+    b = P.Lattice(64, TC, seed=1, init="cold_up")
+    b.set_launch(proc_bits=32, regcap=0, insert=0, block=128, rows_per_item=4, grid=0)
+    Ma, Ea = a.sweep(1000, 1, collect=True)
+    Mb, Eb = b.sweep(1000, 1, collect=True)
+    assert np.array_equal(Ma, Mb) and np.array_equal(Ea, Eb)
+    assert np.array_equal(a.spins(), b.spins())
+
+
+def test_tiny_is_rejected_where_it_does_not_apply(P):
+    for L in (192, 2048):
+        lat = P.Lattice(L, 2.0, seed=1)
+        with pytest.raises(P.IsingError):
+            lat.set_launch(**TINY, block=256)
+        lat.close()
+    lat = P.Lattice(64, 2.0, seed=1)
+    for bad in ({"block": 1024}, {"grid": 2}, {"rows_per_item": 4}, {"regcap": 1}):
+        with pytest.raises(P.IsingError):
+            lat.set_launch(**dict(TINY, block=256, **bad))
+    lat.close()
+
+
+def test_tiny_autotune_and_strips_keep_step_kernels(P, orc):
+    """The autotuner may pick the one-CTA kernel for a small lattice; the strip and
+    allocation-free entry points, which run single steps, still use step kernels."""
+    L, T, seed = 128, TC, 3
+    lat = P.Lattice(L, T, seed=seed)
+    cfg, us = lat.autotune(reps=1)
+    assert cfg in P.ising_launch_candidates(L) and us > 0
+    M, E = lat.sweep(6, 1, collect=True)
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_hot(L, seed)
+    Mo, Eo = orc.run(s, 6, seed, 0, thr4, thr8)
+    assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
