@@ -319,6 +319,17 @@ def extras(P, stream):
     out["field_L32768_H0.1"] = {"attempts_per_ns": 32768 ** 2 * 200 / t_f / 1e9,
                                 "note": "200 sweeps, M/E every sweep, wall time of one call"}
     f.close()
+
+    # the shape of the paper's single-GPU comparison (Table 1): L = 4096 at T = 0.99 T_c
+    w = WL.paper_benchmark()
+    q = P.Lattice(**WL.lattice_kwargs(w))
+    q.autotune(reps=2)
+    t_q = timed_call(q)
+    out["paper_shape_L4096_0.99Tc"] = {
+        "attempts_per_ns": 4096 ** 2 * w["sweeps"] / t_q / 1e9, "launch": q.launch,
+        "note": "1000 sweeps, M/E every sweep, wall time of one call; the paper's best single-GPU "
+                "figure on this shape is 7.98 attempts/ns (Tesla C1060, another RNG): context only"}
+    q.close()
     return out
 
 
@@ -387,22 +398,37 @@ def run_fss(args):
     after 2e5 sweeps (20 % dropped), against Onsager's T_c = 2/ln(1 + sqrt 2)."""
     import math
 
+    import numpy as np
+
     from paper_1007_3726_gb300 import fss
 
+    Ls = (64, 128, 256, 512)
+    if args.fss_long:
+        # sweeps ~ L^2.17 (the Metropolis autocorrelation time at T_c), 2e5 at L = 64;
+        # each lattice of these sizes runs on one CTA, so L = 512 (2e7 sweeps) is left out
+        Ls = (64, 128, 256)
+        sweeps = {L: int(round(2e5 * (L / 64) ** 2.17, -4)) for L in Ls}
+        temps = np.linspace(2.255, 2.285, 16)
+        record_every = 100
+    else:
+        sweeps = {L: args.fss_sweeps for L in Ls}
+        temps = None
+        record_every = 10
     t = time.perf_counter()
-    res = fss.run_fss(sweeps=args.fss_sweeps)
+    res = fss.run_fss(Ls=Ls, temps=temps, sweeps=sweeps, record_every=record_every)
     el = time.perf_counter() - t
     cr = fss.crossings(res)
     tc = 2.0 / math.log(1.0 + math.sqrt(2.0))
-    N = sum(L * L for L in res) * len(next(iter(res.values()))[0])
+    nT = len(next(iter(res.values()))[0])
+    work = sum(L * L * nT * sweeps[L] for L in res)
     line = {"metric": "finite-size-scaling T_c from U4 crossings", "value": cr[-1]["T_cross"],
             "unit": "T", "onsager_tc": tc, "crossings": cr, "seconds": el,
-            "attempts_per_ns": N * args.fss_sweeps / el / 1e9,
+            "attempts_per_ns": work / el / 1e9, "sweeps": {str(L): n for L, n in sweeps.items()},
             "U4": {str(L): [float(x) for x in v[1]] for L, v in res.items()},
             "temps": [float(x) for x in next(iter(res.values()))[0]],
-            "config": {"workload": "L in {64,128,256,512} x 32 T in [2.24, 2.30], cold start, "
-                                   "%d sweeps, sample every 10, 20%% burn-in, block bootstrap"
-                                   % args.fss_sweeps}}
+            "config": {"workload": "L in %s x %d T in [%.3f, %.3f], cold start, sweeps %s, "
+                                   "sample every %d, 20%% burn-in, block bootstrap"
+                                   % (list(Ls), nT, res[64][0][0], res[64][0][-1], sweeps, record_every)}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -566,6 +592,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the L=64 and 128-lattice workloads")
     ap.add_argument("--fss-sweeps", type=int, default=200000)
+    ap.add_argument("--fss-long", action="store_true",
+                    help="--workload fss on L = 64, 128, 256 with sweeps ~ L^2.17 (2e5 at L = 64) "
+                         "on 16 T in [2.255, 2.285]")
     ap.add_argument("--workload", default="default", choices=["default", "largest", "served", "fss"],
                     help="default: L=32768 (the benchmark line); largest: L=524288; served: request stream")
     args = ap.parse_args()

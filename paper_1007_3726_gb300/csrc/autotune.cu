@@ -41,7 +41,8 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
         auto it = g_tuned.find(std::make_tuple(device, L, word_bits));
         if (it != g_tuned.end()) return it->second;
     }
-    if (L <= 256 && tiny_lattice_ok(L)) return LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 1};
+    // one CTA for small lattices (L = 64 has 128 words: one per thread)
+    if (L <= 128 && tiny_lattice_ok(L)) return LaunchConfig{kTinyProcBits, 0, 0, L == 64 ? 128u : 512u, 1, 1};
     LaunchConfig c{64, 1, 1, 512, 8, 0};
     return c;
 }

@@ -3,15 +3,13 @@
 // launches (Sec. 5.2 needs one global synchronisation per checkerboard step;
 // for a lattice that one CTA holds, a CTA barrier is that synchronisation).
 //
-// One thread per byte of the packed lattice: a byte of a row holds four target
-// sites of a step, exactly the sites of one Philox4x32-10 call, so thread b
-// owns Philox group b (= y L/8 + q for byte q of row y) and writes only its
-// own byte.  The update of the byte is the update of Sec. 4 on eight bits:
-// the neighbour bytes above and below, the row byte shifted by one with the
-// carry bit from the adjacent byte, the bit-sliced count, the two threshold
-// masks and the masked XOR.  Bits a thread reads from its neighbours' bytes
-// at its own target positions are of the other parity, which nobody writes
-// during the step.
+// The lattice is kept as 32-bit words, W = L / 32 per row; a thread updates
+// whole words with the word update of the step kernel (Sec. 4: neighbour words,
+// bit-sliced count, one Philox4x32-10 call per byte of the word, masked XOR),
+// so the neighbour logic is shared by the word's 16 target sites and its four
+// Philox calls are independent chains.  Bits a thread reads from its
+// neighbours' words at its own target positions are of the other parity, which
+// nobody writes during the step.
 #include "kernels.h"
 #include "sweep_device.cuh"
 
@@ -23,17 +21,17 @@ constexpr uint32_t kTinyMaxThreads = 512;
 
 __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant__ TinyRunArgs A)
 {
-    extern __shared__ uint32_t smw[];
+    extern __shared__ uint32_t lat[];
     __shared__ unsigned int cnt[2];
-    uint8_t *const lat = reinterpret_cast<uint8_t *>(smw);
     const uint32_t L = (uint32_t)A.L;
-    const uint32_t BPR = L >> 3;                 // bytes per row, a power of two
-    const uint32_t lgB = 31 - __clz(BPR);
-    const uint32_t nbytes = L * BPR;
+    const uint32_t W = L >> 5;                  // words per row, a power of two
+    const uint32_t lgW = 31 - __clz(W);
+    const uint32_t nwords = L * W;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const uint64_t groups_per_row = L >> 3;
 
     const uint32_t *src = static_cast<const uint32_t *>(A.spins);
-    for (uint32_t i = tid; i < nbytes / 4; i += nthr) smw[i] = src[i];
+    for (uint32_t i = tid; i < nwords; i += nthr) lat[i] = src[i];
     if (tid < 2) cnt[tid] = 0u;
     __syncthreads();
 
@@ -60,44 +58,16 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
             a.r1x2k = (A.c3base | p) ^ A.key.k1[0];
             const bool count = p == 1u && (rec || last);
             unsigned int cu = 0, ca = 0;
-            for (uint32_t b = tid; b < nbytes; b += nthr) {
-                const uint32_t y = b >> lgB, q = b & (BPR - 1u);
-                const uint32_t rowb = b - q;
-                const uint32_t up = lat[(y == 0 ? nbytes - BPR : rowb - BPR) + q];
-                const uint32_t dn = lat[(y + 1 == L ? 0u : rowb + BPR) + q];
-                const uint32_t cur = lat[b];
-                const uint32_t lb = lat[rowb + ((q - 1u) & (BPR - 1u))];
-                const uint32_t rb = lat[rowb + ((q + 1u) & (BPR - 1u))];
-                const uint32_t left = ((cur << 1) | (lb >> 7)) & 0xFFu;  // bit k holds s(x - 1)
-                const uint32_t right = (cur >> 1) | ((rb & 1u) << 7);     // bit k holds s(x + 1)
-                const uint32_t off = (y + p) & 1u;
-                const uint32_t mask = 0x55u << off;
-
-                const uint32_t i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
-                const uint32_t s12 = i1 ^ i2, c12 = i1 & i2;
-                const uint32_t s34 = i3 ^ i4, c34 = i3 & i4;
-                const uint32_t odd = s12 ^ s34;
-                const uint32_t ge2 = c12 | c34 | (s12 & s34);
-                const uint32_t eq1 = odd & ~ge2;
-                const uint32_t eq0 = ~(odd | ge2);
-
-                const WordDraws d = word_draws_begin(a, (uint64_t)b);
-                uint32_t u[4];
-                word_draw_call(a, d, 0u, u);
-                uint32_t p4 = 0u, p8 = 0u;
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    p4 |= (u[l] < a.thr4) ? (1u << (2 * l)) : 0u;
-                    p8 |= (u[l] < a.thr8) ? (1u << (2 * l)) : 0u;
-                }
-                const uint32_t flip = mask & (ge2 | (eq1 & (p4 << off)) | (eq0 & (p8 << off)));
-                const uint32_t nw = cur ^ flip;
-                lat[b] = (uint8_t)nw;
-                if (count) {
-                    cu += __popc(nw);
-                    ca += __popc(mask & (nw ^ up)) + __popc(mask & (nw ^ dn)) + __popc(mask & (nw ^ left)) +
-                          __popc(mask & (nw ^ right));
-                }
+            for (uint32_t k = tid; k < nwords; k += nthr) {
+                const uint32_t y = k >> lgW, w = k & (W - 1u);
+                const uint32_t row = k - w;
+                const uint32_t cur = lat[k];
+                const uint32_t up = lat[(y == 0 ? nwords - W : row - W) + w];
+                const uint32_t dn = lat[(y + 1 == L ? 0u : row + W) + w];
+                const uint32_t lw = lat[row + ((w - 1u) & (W - 1u))];
+                const uint32_t rw = lat[row + ((w + 1u) & (W - 1u))];
+                const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
+                lat[k] = update_word<uint32_t, 0>(a, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca);
             }
             if (count) {
                 cu = __reduce_add_sync(0xFFFFFFFFu, cu);
@@ -128,7 +98,7 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
     }
     __syncthreads();
     uint32_t *dst = static_cast<uint32_t *>(A.spins);
-    for (uint32_t i = tid; i < nbytes / 4; i += nthr) dst[i] = smw[i];
+    for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = lat[i];
 }
 
 }  // namespace

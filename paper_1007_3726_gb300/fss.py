@@ -38,23 +38,29 @@ def bootstrap_binder(M: np.ndarray, N: float, nblocks: int = 50, nboot: int = 20
 
 def run_fss(Ls=(64, 128, 256, 512), temps=None, sweeps=200000, record_every=10, burn_frac=0.2,
             seed=3, init="cold_up", batch_opts=None):
-    """U4(L, T) from one persistent batch; returns {L: (temps, U4, U4_boot[nboot, nT])}."""
+    """U4(L, T) from one persistent batch; returns {L: (temps, U4, U4_boot[nboot, nT])}.
+
+    `sweeps` is one count for every size or a {L: sweeps} map (critical slowing
+    down: the autocorrelation time of the Metropolis update grows about as
+    L^2.17 at T_c, so larger lattices need more sweeps)."""
     import paper_1007_3726_gb300 as P
 
     if temps is None:
         temps = np.linspace(2.24, 2.30, 32)
-    lats, keys = [], []
+    per_L = sweeps if isinstance(sweeps, dict) else {L: sweeps for L in Ls}
+    lats, keys, ns = [], [], []
     for iL, L in enumerate(Ls):
         for iT, T in enumerate(temps):
             lats.append(P.Lattice(L, float(T), seed=seed, stream_id=64 * iL + iT, init=init))
             keys.append((L, iT))
+            ns.append(int(per_L[L]))
     opts = dict(batch_opts or {})
-    with P.Batch(lats, [sweeps] * len(lats), record_every, **opts) as b:
+    with P.Batch(lats, ns, record_every, **opts) as b:
         b.run(1)
-    burn = int(burn_frac * sweeps / record_every)
     out = {}
     rng = np.random.default_rng(12345)
     for (L, iT), lat in zip(keys, lats):
+        burn = int(burn_frac * per_L[L] / record_every)
         M, _ = lat.samples(first=burn)
         u, reps = bootstrap_binder(M, float(L) * L, rng=rng)
         d = out.setdefault(L, [np.asarray(temps, dtype=np.float64), np.zeros(len(temps)),

@@ -91,8 +91,10 @@ def test_tiny_is_rejected_where_it_does_not_apply(P):
         lat.close()
     lat = P.Lattice(64, 2.0, seed=1)
     for bad in ({"block": 1024}, {"grid": 2}, {"rows_per_item": 4}, {"regcap": 1}):
+        cfg = dict(TINY, block=256)
+        cfg.update(bad)
         with pytest.raises(P.IsingError):
-            lat.set_launch(**dict(TINY, block=256, **bad))
+            lat.set_launch(**cfg)
     lat.close()
 
 
