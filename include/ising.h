@@ -218,6 +218,13 @@ ISING_API const char *ising_last_error(void);
  *   insert         0, 1 or 2: how many of the two acceptance masks (u < thr4,
  *                  u < thr8) are built with logic operations rather than
  *                  additions (a balance between two integer pipelines)
+ * proc_bits = 8 selects instead the one-CTA form for lattices one thread block
+ * holds (L a power of two, 64 <= L <= 1024): the whole lattice stays in shared
+ * memory and every sweep of an ising_sweep call runs in one launch, with a
+ * block barrier as the synchronisation between steps A and B.  Then block is
+ * its size, rows_per_item the threads that share one 32-bit word (1, 2 or 4),
+ * regcap = insert = 0 and grid = 1.  It is the default for L <= 256; a field
+ * (H != 0) always runs the field kernel.
  */
 typedef struct {
     uint32_t proc_bits, regcap, block, rows_per_item, grid, insert;
@@ -231,7 +238,8 @@ ISING_API ising_status ising_set_launch(ising_lattice *h, const ising_launch *cf
  * returns how many there are in total (out may be NULL to count). */
 ISING_API uint32_t ising_launch_candidates(uint64_t L, ising_launch *out, uint32_t cap);
 /*
- * Times every candidate (reps timed step pairs each, after one untimed pair)
+ * Times every candidate (reps timed step pairs each, after one untimed pair;
+ * a one-CTA candidate: one launch of 8 reps sweeps after a one-sweep launch)
  * on a scratch copy of up to 256 MiB of the handle's rows, installs the
  * fastest on the handle, remembers it for later handles of the same L and
  * word width on this device, and returns it with its mean time per step in

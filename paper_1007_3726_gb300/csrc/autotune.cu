@@ -41,8 +41,9 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
         auto it = g_tuned.find(std::make_tuple(device, L, word_bits));
         if (it != g_tuned.end()) return it->second;
     }
-    // one CTA for small lattices (L = 64 has 128 words: one per thread)
-    if (L <= 128 && tiny_lattice_ok(L)) return LaunchConfig{kTinyProcBits, 0, 0, L == 64 ? 128u : 512u, 1, 1};
+    // one CTA for small lattices (the fastest shapes measured at L = 64, 128, 256)
+    if (L <= 256 && tiny_lattice_ok(L))
+        return L == 64 ? LaunchConfig{kTinyProcBits, 0, 0, 256, 2, 1} : LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 1};
     LaunchConfig c{64, 1, 1, 512, 8, 0};
     return c;
 }
@@ -57,10 +58,11 @@ std::vector<LaunchConfig> launch_candidates(uint64_t L, uint64_t rows)
 {
     std::vector<LaunchConfig> out;
     // the one-CTA kernel, for lattices one CTA holds
-    for (uint32_t blk : {128u, 256u, 512u}) {
-        LaunchConfig c{kTinyProcBits, 0, 0, blk, 1, 1};
-        if (launch_config_valid(c, L, rows)) out.push_back(c);
-    }
+    for (uint32_t blk : {128u, 256u, 512u})
+        for (uint32_t tpw : {1u, 2u, 4u}) {
+            LaunchConfig c{kTinyProcBits, 0, 0, blk, tpw, 1};
+            if (launch_config_valid(c, L, rows)) out.push_back(c);
+        }
     for (uint32_t pb : {32u, 64u})
         for (uint32_t rc : {0u, 1u, 2u})
             for (uint32_t ins : {0u, 1u, 2u})
@@ -171,10 +173,10 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
             ta.nrec = 0;
             ta.acc = h->d_acc;
             ta.nsweeps = 1;
-            e = launch_tiny(ta, c.block, h->stream);
+            e = launch_tiny(ta, c.block, c.rows_per_item, h->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
             ta.nsweeps = 8 * reps;
-            if (e == cudaSuccess) e = launch_tiny(ta, c.block, h->stream);
+            if (e == cudaSuccess) e = launch_tiny(ta, c.block, c.rows_per_item, h->stream);
             steps = 16 * reps;
         }
         for (uint32_t r = 0; r <= reps && e == cudaSuccess && c.proc_bits != kTinyProcBits; ++r) {

@@ -415,7 +415,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
         ta.record_every = record_every;
         ta.nrec = (uint32_t)nrec;
         ta.acc = h->d_acc;
-        CK(h, launch_tiny(ta, h->launch.block, h->stream));
+        CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->stream));
         return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
     }
     HalfSweepArgs a{};

@@ -55,8 +55,8 @@ void prepare_half_sweep(HalfSweepArgs &a, int grid, int block);
 // A launch configuration of the half-sweep.  Every valid configuration gives
 // bit-identical results; they differ only in speed.  proc_bits == 8 selects the
 // one-CTA kernel of tiny.cu instead (whole lattice in shared memory, every
-// sweep of a call in one launch; only block is used, the other fields are 0,
-// 0, 1, 1).
+// sweep of a call in one launch): block is its block size, rows_per_item the
+// threads that share one 32-bit word (1, 2 or 4), regcap = insert = 0, grid = 1.
 struct LaunchConfig {
     uint32_t proc_bits;      // 32 or 64: bits one thread updates per row; 8: one CTA
     uint32_t regcap;         // 0: compiler's choice, 1: <= 40 registers, 2: <= 32 registers
@@ -91,7 +91,7 @@ struct TinyRunArgs {
     uint32_t nrec;            // recorded sweeps of the call
     unsigned long long *acc;  // nrec + 1 slots of two counters
 };
-cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, cudaStream_t s);
+cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, cudaStream_t s);
 // Resident blocks per SM of the configuration's kernel.
 int half_sweep_blocks_per_sm(const LaunchConfig &c);
 // Grid that makes every block resident (grid == 0 resolved).

@@ -7,9 +7,11 @@
 // whole words with the word update of the step kernel (Sec. 4: neighbour words,
 // bit-sliced count, one Philox4x32-10 call per byte of the word, masked XOR),
 // so the neighbour logic is shared by the word's 16 target sites and its four
-// Philox calls are independent chains.  Bits a thread reads from its
-// neighbours' words at its own target positions are of the other parity, which
-// nobody writes during the step.
+// Philox calls are independent chains.  For very small lattices S = 2 or 4
+// threads share a word (each draws 4 / S of its calls and stores only its own
+// bytes), so that more warps hide the latency of a step.  Bits a thread reads
+// from its neighbours' words at its own target positions are of the other
+// parity, which nobody writes during the step.
 #include "kernels.h"
 #include "sweep_device.cuh"
 
@@ -19,8 +21,10 @@ namespace {
 
 constexpr uint32_t kTinyMaxThreads = 512;
 
+template <int NQ>  // Philox calls (bytes) per thread: 4, 2 or 1
 __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant__ TinyRunArgs A)
 {
+    constexpr uint32_t S = 4 / NQ;  // threads per word
     extern __shared__ uint32_t lat[];
     __shared__ unsigned int cnt[2];
     const uint32_t L = (uint32_t)A.L;
@@ -58,7 +62,8 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
             a.r1x2k = (A.c3base | p) ^ A.key.k1[0];
             const bool count = p == 1u && (rec || last);
             unsigned int cu = 0, ca = 0;
-            for (uint32_t k = tid; k < nwords; k += nthr) {
+            for (uint32_t it = tid; it < nwords * S; it += nthr) {
+                const uint32_t k = it / S, sub = it % S;  // S is a power of two
                 const uint32_t y = k >> lgW, w = k & (W - 1u);
                 const uint32_t row = k - w;
                 const uint32_t cur = lat[k];
@@ -67,7 +72,14 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
                 const uint32_t lw = lat[row + ((w - 1u) & (W - 1u))];
                 const uint32_t rw = lat[row + ((w + 1u) & (W - 1u))];
                 const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
-                lat[k] = update_word<uint32_t, 0>(a, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca);
+                const uint32_t nw = update_word<uint32_t, 0, NQ>(a, cur, up, dn, lw, rw, (y + p) & 1u, g, count,
+                                                                  cu, ca, sub * NQ);
+                if (NQ == 4)
+                    lat[k] = nw;
+                else if (NQ == 2)
+                    reinterpret_cast<uint16_t *>(lat + k)[sub] = (uint16_t)(nw >> (16 * sub));
+                else
+                    reinterpret_cast<uint8_t *>(lat + k)[sub] = (uint8_t)(nw >> (8 * sub));
             }
             if (count) {
                 cu = __reduce_add_sync(0xFFFFFFFFu, cu);
@@ -103,16 +115,20 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
 
 }  // namespace
 
-cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, cudaStream_t s)
+cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, cudaStream_t s)
 {
     if (!tiny_lattice_ok(a.L) || a.nsweeps == 0 || block == 0 || block > kTinyMaxThreads || block % 32 != 0)
         return cudaErrorInvalidValue;
+    void (*kern)(TinyRunArgs) = threads_per_word == 1 ? k_tiny<4>
+                                : threads_per_word == 2 ? k_tiny<2>
+                                : threads_per_word == 4 ? k_tiny<1> : nullptr;
+    if (!kern) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(a.L * a.L / 8);
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(k_tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_tiny<<<1, block, smem, s>>>(a);
+    kern<<<1, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 

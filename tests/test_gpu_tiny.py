@@ -24,16 +24,17 @@ def P():
     return P
 
 
-TINY = {"proc_bits": 8, "regcap": 0, "insert": 0, "rows_per_item": 1, "grid": 1}
+TINY = {"proc_bits": 8, "regcap": 0, "insert": 0, "grid": 1}
 
 
 @pytest.mark.parametrize("L", [64, 128, 256, 512, 1024])
 @pytest.mark.parametrize("block", [128, 256, 512])
-def test_tiny_sizes_and_blocks_bit_exact(P, orc, L, block):
-    n = 12 if L <= 256 else 4
-    T, seed, sid = TC, L + block, 1
+@pytest.mark.parametrize("tpw", [1, 2, 4])
+def test_tiny_sizes_blocks_and_threads_per_word_bit_exact(P, orc, L, block, tpw):
+    n = 12 if L <= 256 else 3
+    T, seed, sid = TC, L + block + tpw, 1
     lat = P.Lattice(L, T, seed=seed, stream_id=sid, init="hot", word_bits=64 if L >= 512 else 32)
-    lat.set_launch(**TINY, block=block)
+    lat.set_launch(**TINY, block=block, rows_per_item=tpw)
     assert lat.launch["proc_bits"] == 8
     M, E = lat.sweep(n, 1, collect=True)
     thr4, thr8 = orc.thresholds(T)
@@ -51,7 +52,7 @@ def test_tiny_split_calls_sparse_records_and_final_state(P, orc, T):
     crosses call boundaries); calls with no sample still update M and E."""
     L, seed = 128, 41
     lat = P.Lattice(L, T, seed=seed, init="cold_up")
-    lat.set_launch(**TINY, block=256)
+    lat.set_launch(**TINY, block=256, rows_per_item=2)
     Ms, Es = [], []
     for n in (7, 13, 1, 39, 2):
         M, E = lat.sweep(n, 3, collect=True)
@@ -87,11 +88,11 @@ def test_tiny_is_rejected_where_it_does_not_apply(P):
     for L in (192, 2048):
         lat = P.Lattice(L, 2.0, seed=1)
         with pytest.raises(P.IsingError):
-            lat.set_launch(**TINY, block=256)
+            lat.set_launch(**TINY, block=256, rows_per_item=1)
         lat.close()
     lat = P.Lattice(64, 2.0, seed=1)
-    for bad in ({"block": 1024}, {"grid": 2}, {"rows_per_item": 4}, {"regcap": 1}):
-        cfg = dict(TINY, block=256)
+    for bad in ({"block": 1024}, {"grid": 2}, {"rows_per_item": 3}, {"rows_per_item": 8}, {"regcap": 1}):
+        cfg = dict(TINY, block=256, rows_per_item=1)
         cfg.update(bad)
         with pytest.raises(P.IsingError):
             lat.set_launch(**cfg)
