@@ -251,20 +251,9 @@ void prepare_half_sweep(HalfSweepArgs &a, int grid, int block)
     a.stride_w = (uint32_t)(stride % a.words_per_row);
 }
 
-bool tiny_lattice_ok(uint64_t L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
-
-LaunchConfig plain_launch(const LaunchConfig &c)
-{
-    if (c.proc_bits == 32 || c.proc_bits == 64) return c;
-    return LaunchConfig{64, 1, 1, 512, 8, 0};
-}
-
 bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
-    if (c.proc_bits == kTinyProcBits)
-        return tiny_lattice_ok(L) && rows == L && c.regcap == 0 && c.insert == 0 &&
-               (c.block == 128 || c.block == 256 || c.block == 512) &&
-               (c.rows_per_item == 1 || c.rows_per_item == 2 || c.rows_per_item == 4) && c.grid == 1;
+    if (c.proc_bits == kTinyProcBits) return tiny_config_valid(c, L, rows);
     if (c.proc_bits != 32 && c.proc_bits != 64) return false;
     if (c.regcap > 2) return false;
     if (c.insert > 2) return false;

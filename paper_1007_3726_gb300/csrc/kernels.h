@@ -71,6 +71,8 @@ bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows);
 constexpr uint32_t kTinyProcBits = 8;
 // Lattices the one-CTA kernel takes: L a power of two, 64 <= L <= 1024.
 bool tiny_lattice_ok(uint64_t L);
+// A one-CTA configuration (proc_bits == 8) for an L x L lattice of `rows` rows.
+bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows);
 // c itself if it is a configuration of the half-sweep kernel, else the fixed
 // default one (for callers that launch single steps).
 LaunchConfig plain_launch(const LaunchConfig &c);

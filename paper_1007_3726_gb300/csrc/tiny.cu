@@ -115,6 +115,21 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
 
 }  // namespace
 
+bool tiny_lattice_ok(uint64_t L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
+
+bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
+{
+    return c.proc_bits == kTinyProcBits && tiny_lattice_ok(L) && rows == L && c.regcap == 0 && c.insert == 0 &&
+           (c.block == 128 || c.block == 256 || c.block == 512) &&
+           (c.rows_per_item == 1 || c.rows_per_item == 2 || c.rows_per_item == 4) && c.grid == 1;
+}
+
+LaunchConfig plain_launch(const LaunchConfig &c)
+{
+    if (c.proc_bits == 32 || c.proc_bits == 64) return c;
+    return LaunchConfig{64, 1, 1, 512, 8, 0};
+}
+
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, cudaStream_t s)
 {
     if (!tiny_lattice_ok(a.L) || a.nsweeps == 0 || block == 0 || block > kTinyMaxThreads || block % 32 != 0)
