@@ -5,7 +5,8 @@
  * Model" (arXiv:1007.3726).
  *
  * Model (Sec. 3, Eq. 1): spins S = +1 / -1 on an L x L square lattice with
- * periodic boundaries, H = -J sum_<ij> S_i S_j with J = 1 and no field.
+ * periodic boundaries, H = -J sum_<ij> S_i S_j - H sum_i S_i with J = 1; the
+ * paper's case is H = 0 (a field is optional, see ising_set_field).
  * Dynamics (Sec. 3): Metropolis, checkerboard order: step A updates the sites
  * with (x + y) even, then step B the sites with (x + y) odd; a sweep is A then
  * B.  A move with dE <= 0 is always accepted; dE = 4 or 8 is accepted when the
@@ -91,7 +92,7 @@ typedef struct {
     uint64_t first_sweep;   /* sweeps already applied to the initial state (resuming a saved
                                lattice: the next sweep uses Philox counter word 2 = first_sweep) */
     double H;               /* external field of Sec. 3, Eq. 1 (finite; 0 = the paper's case).
-                               A nonzero field runs the field kernel of ising_sweep; the
+                               A nonzero field runs the field update of ising_sweep; the
                                recorded E stays the bond energy -sum S_i S_j (the field
                                energy is -H M) */
 } ising_params;
@@ -223,8 +224,9 @@ ISING_API const char *ising_last_error(void);
  * memory and every sweep of an ising_sweep call runs in one launch, with a
  * block barrier as the synchronisation between steps A and B.  Then block is
  * its size, rows_per_item the threads that share one 32-bit word (1, 2 or 4),
- * regcap = insert = 0 and grid = 1.  It is the default for L <= 256; a field
- * (H != 0) always runs the field kernel.
+ * regcap = insert = 0 and grid = 1.  It is the default for L <= 256.  In a
+ * field (H != 0) it uses one thread per word whatever rows_per_item says; the
+ * step kernels are then replaced by the field step kernel.
  */
 typedef struct {
     uint32_t proc_bits, regcap, block, rows_per_item, grid, insert;

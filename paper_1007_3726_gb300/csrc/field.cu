@@ -20,74 +20,13 @@
 // Lattices are processed 32 bits at a time whatever their storage width (a
 // 64-bit word is two consecutive 32-bit words).
 #include "field.h"
-#include "sweep_device.cuh"
+#include "field_device.cuh"
+
+#include <atomic>
 
 namespace ising {
 
 namespace {
-
-constexpr uint32_t kEven = 0x55555555u;
-
-// Sites with c >= k, for a uniform k in 0..5 (c = b0 + 2 b1 + 4 b2 <= 4).
-__device__ __forceinline__ uint32_t count_at_least(uint32_t k, uint32_t b0, uint32_t b1, uint32_t b2)
-{
-    return k == 0 ? ~0u : k == 1 ? (b0 | b1 | b2) : k == 2 ? (b1 | b2) : k == 3 ? ((b0 & b1) | b2)
-           : k == 4 ? b2 : 0u;
-}
-
-// One 32-bit word of target sites (see update_word for the arguments); tab is
-// the 16-entry threshold table in shared memory, index 8 S + c.
-__device__ __forceinline__ uint32_t update_word_field(const HalfSweepArgs &a, const uint32_t *tab,
-                                                      uint32_t k_up, uint32_t k_dn, uint32_t cur,
-                                                      uint32_t up, uint32_t dn, uint32_t lw, uint32_t rw,
-                                                      uint32_t off, uint64_t g, bool count,
-                                                      unsigned int &cnt_up, unsigned int &cnt_anti)
-{
-    const uint32_t left = (cur << 1) | (lw >> 31);   // bit b holds s(x - 1)
-    const uint32_t right = (cur >> 1) | (rw << 31);  // bit b holds s(x + 1)
-    const uint32_t mask = off ? (kEven << 1) : kEven;
-
-    // energy variables and the three bits of their sum c
-    const uint32_t i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
-    const uint32_t s12 = i1 ^ i2, c12 = i1 & i2;
-    const uint32_t s34 = i3 ^ i4, c34 = i3 & i4;
-    const uint32_t b0 = s12 ^ s34;
-    const uint32_t b1 = c12 ^ c34 ^ (s12 & s34);
-    const uint32_t b2 = c12 & c34;  // c == 4 (then s12 = s34 = 0)
-    const uint32_t always = (cur & count_at_least(k_up, b0, b1, b2)) |
-                            (~cur & count_at_least(k_dn, b0, b1, b2));
-
-    // the class of target site j (bit off + 2j) as two 2-bit fields at bit 2j:
-    // X = (b1 b0), Y = (S b2); its table index is X_j | Y_j << 2
-    const uint32_t X = ((b0 >> off) & kEven) | (((b1 >> off) & kEven) << 1);
-    const uint32_t Y = ((b2 >> off) & kEven) | (((cur >> off) & kEven) << 1);
-
-    const WordDraws d = word_draws_begin(a, g);
-    uint32_t P = a.zero;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint32_t u[4];
-        word_draw_call(a, d, (uint32_t)q, u);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const int pos = 8 * q + 2 * l;
-            const uint32_t idx = ((X >> pos) & 3u) | (((Y >> pos) & 3u) << 2);
-            const uint32_t thr = tab[idx];
-            const uint32_t bit = 1u << pos;
-            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
-                : "+r"(P)
-                : "r"(u[l]), "r"(thr), "r"(bit));
-        }
-    }
-    const uint32_t flip = mask & (always | (P << off));
-    const uint32_t nw = cur ^ flip;
-    if (count) {
-        cnt_up += __popc(nw);
-        cnt_anti += __popc(mask & (nw ^ up)) + __popc(mask & (nw ^ dn)) + __popc(mask & (nw ^ left)) +
-                    __popc(mask & (nw ^ right));
-    }
-    return nw;
-}
 
 // Work item = (block of R rows, word column); the thread walks down its column
 // as in the zero-field kernel.  Whole periodic lattice.  Three blocks of 512 per
@@ -142,6 +81,7 @@ __global__ void __launch_bounds__(512, 3) k_half_sweep_field(const __grid_consta
 }
 
 constexpr int kFieldBlock = 512;
+constexpr int kMaxDevices = 64;
 
 }  // namespace
 
@@ -177,16 +117,21 @@ cudaError_t launch_half_sweep_field(HalfSweepArgs a, const FieldTable &ft, cudaS
     a.words_per_row = (uint32_t)(a.L / 32);
     a.rows_per_item = 8;  // L is a multiple of 64
     a.zero = 0u;
-    int dev = 0, sms = 0, per_sm = 0;
+    // resident blocks of the device, queried once per device
+    static std::atomic<int> resident[kMaxDevices];
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_half_sweep_field, kFieldBlock, 0);
-    if (per_sm <= 0) per_sm = 1;
-    if (sms <= 0) sms = 1;
+    int cap = (dev >= 0 && dev < kMaxDevices) ? resident[dev].load(std::memory_order_relaxed) : 0;
+    if (cap <= 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_half_sweep_field, kFieldBlock, 0);
+        cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        if (dev >= 0 && dev < kMaxDevices) resident[dev].store(cap, std::memory_order_relaxed);
+    }
     const uint64_t items = (a.L / 8) * (uint64_t)a.words_per_row;
     const uint64_t need = (items + kFieldBlock - 1) / kFieldBlock;
-    const uint64_t cap = (uint64_t)sms * (uint64_t)per_sm;
-    const int grid = (int)(need < cap ? need : cap);
+    const int grid = (int)(need < (uint64_t)cap ? need : (uint64_t)cap);
     prepare_half_sweep(a, grid, kFieldBlock);
     k_half_sweep_field<<<grid, kFieldBlock, 0, s>>>(a, ft);
     return cudaGetLastError();

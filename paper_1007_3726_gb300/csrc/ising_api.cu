@@ -401,7 +401,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
     if ((st = ensure_acc(h, nrec + 1)) != ISING_OK) return st;
 
     CK(h, cudaMemsetAsync(h->d_acc, 0, (nrec + 1) * 16, h->stream));
-    if (h->launch.proc_bits == kTinyProcBits && h->H == 0.0) {
+    if (h->launch.proc_bits == kTinyProcBits) {
         // the whole call in one launch of one CTA
         TinyRunArgs ta{};
         ta.spins = h->d_spins;
@@ -415,6 +415,12 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
         ta.record_every = record_every;
         ta.nrec = (uint32_t)nrec;
         ta.acc = h->d_acc;
+        if (h->H != 0.0) {
+            ta.use_field = 1;
+            for (int k = 0; k < 16; ++k) ta.field_thr[k] = h->field.thr[k];
+            ta.k_up = h->field.k_up;
+            ta.k_dn = h->field.k_dn;
+        }
         CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->stream));
         return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
     }

@@ -92,6 +92,11 @@ struct TinyRunArgs {
     uint32_t record_every;    // 0: record nothing
     uint32_t nrec;            // recorded sweeps of the call
     unsigned long long *acc;  // nrec + 1 slots of two counters
+    // in a field H != 0 (use_field = 1): the class thresholds and the always-
+    // accepted classes of field.h's FieldTable (thr4 / thr8 are then unused)
+    uint32_t use_field;
+    uint32_t field_thr[16];
+    uint32_t k_up, k_dn;
 };
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, cudaStream_t s);
 // Resident blocks per SM of the configuration's kernel.

@@ -9,9 +9,12 @@
 // so the neighbour logic is shared by the word's 16 target sites and its four
 // Philox calls are independent chains.  For very small lattices S = 2 or 4
 // threads share a word (each draws 4 / S of its calls and stores only its own
-// bytes), so that more warps hide the latency of a step.  Bits a thread reads
+// bytes), so that more warps hide the latency of a step.  In a field H the
+// word update is the ten-class one of field_device.cuh (one thread per word,
+// the class thresholds in shared memory).  Bits a thread reads
 // from its neighbours' words at its own target positions are of the other
 // parity, which nobody writes during the step.
+#include "field_device.cuh"
 #include "kernels.h"
 #include "sweep_device.cuh"
 
@@ -21,12 +24,15 @@ namespace {
 
 constexpr uint32_t kTinyMaxThreads = 512;
 
-template <int NQ>  // Philox calls (bytes) per thread: 4, 2 or 1
+template <int NQ, bool FIELD>  // Philox calls (bytes) per thread: 4, 2 or 1; field update
 __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant__ TinyRunArgs A)
 {
+    static_assert(!FIELD || NQ == 4, "the field update takes whole words");
     constexpr uint32_t S = 4 / NQ;  // threads per word
     extern __shared__ uint32_t lat[];
     __shared__ unsigned int cnt[2];
+    __shared__ uint32_t tab[16];
+    if (FIELD && threadIdx.x < 16) tab[threadIdx.x] = A.field_thr[threadIdx.x];
     const uint32_t L = (uint32_t)A.L;
     const uint32_t W = L >> 5;                  // words per row, a power of two
     const uint32_t lgW = 31 - __clz(W);
@@ -72,8 +78,9 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
                 const uint32_t lw = lat[row + ((w - 1u) & (W - 1u))];
                 const uint32_t rw = lat[row + ((w + 1u) & (W - 1u))];
                 const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
-                const uint32_t nw = update_word<uint32_t, 0, NQ>(a, cur, up, dn, lw, rw, (y + p) & 1u, g, count,
-                                                                  cu, ca, sub * NQ);
+                const uint32_t nw =
+                    FIELD ? update_word_field(a, tab, A.k_up, A.k_dn, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca)
+                          : update_word<uint32_t, 0, NQ>(a, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca, sub * NQ);
                 if (NQ == 4)
                     lat[k] = nw;
                 else if (NQ == 2)
@@ -134,9 +141,10 @@ cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_p
 {
     if (!tiny_lattice_ok(a.L) || a.nsweeps == 0 || block == 0 || block > kTinyMaxThreads || block % 32 != 0)
         return cudaErrorInvalidValue;
-    void (*kern)(TinyRunArgs) = threads_per_word == 1 ? k_tiny<4>
-                                : threads_per_word == 2 ? k_tiny<2>
-                                : threads_per_word == 4 ? k_tiny<1> : nullptr;
+    void (*kern)(TinyRunArgs) = a.use_field                ? k_tiny<4, true>
+                                : threads_per_word == 1 ? k_tiny<4, false>
+                                : threads_per_word == 2 ? k_tiny<2, false>
+                                : threads_per_word == 4 ? k_tiny<1, false> : nullptr;
     if (!kern) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(a.L * a.L / 8);
     if (smem > 48 * 1024) {

@@ -111,3 +111,25 @@ def test_tiny_autotune_and_strips_keep_step_kernels(P, orc):
     s = orc.init_hot(L, seed)
     Mo, Eo = orc.run(s, 6, seed, 0, thr4, thr8)
     assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
+
+
+@pytest.mark.parametrize("L", [64, 256, 1024])
+@pytest.mark.parametrize("H", [0.3, -2.0, 5.0])
+def test_tiny_in_a_field_bit_exact(P, orc, L, H):
+    """The one-CTA kernel in a field (ten classes, one thread per word whatever the
+    configuration's threads per word) against the oracle's field update."""
+    n = 10 if L <= 256 else 3
+    T, seed = 2.1, L + 17
+    lat = P.Lattice(L, T, seed=seed, init="hot", H=H)
+    lat.set_launch(**TINY, block=256, rows_per_item=4)
+    M, E = lat.sweep(n, 1, collect=True)
+    s = orc.init_hot(L, seed, 0)
+    Mo, Eo = orc.run_field(s, n, seed, 0, T, H)
+    assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
+    assert np.array_equal(lat.spins(), s)
+    # a change of the field between calls keeps the one-CTA path
+    lat.set_field(-H)
+    M2, _ = lat.sweep(4, 2, collect=True)
+    Mo2, _ = orc.run_field(s, 4, seed, 0, T, -H, t0=n)
+    assert np.array_equal(M2, Mo2[1::2])
+    assert np.array_equal(lat.spins(), s)
