@@ -228,7 +228,6 @@ __device__ void whole_lattices_steps(const BatchLaunchArgs &A, const BatchStrip 
     __syncthreads();
     for (uint32_t s = 0; s < A.max_steps; ++s) {
         const uint32_t p = s & 1u;
-        bool any_count = false;
         for (uint32_t k = 0; k < ns; ++k) {
             const BatchStrip &st = sst[k];
             if (s >= st.nsteps) continue;
@@ -237,7 +236,6 @@ __device__ void whole_lattices_steps(const BatchLaunchArgs &A, const BatchStrip 
             strip_step_args(a, st, t, p);
             const bool recorded = p == 1u && st.record_every != 0u && rec_phase[k] == 0u;
             const bool count = p == 1u && (recorded || s + 1 == st.nsteps);
-            any_count |= count;
             const uint32_t R = strip_R[k], S = strip_S[k];
             const uint32_t lr = 31 - __clz(R);  // R and S are powers of two
             const uint32_t items = ((st.nrows + R - 1) >> lr) * st.W * S;
@@ -286,7 +284,6 @@ __device__ void whole_lattices_steps(const BatchLaunchArgs &A, const BatchStrip 
                 if (st.record_every != 0u) rec_phase[tid] = (rec_phase[tid] + 1 == st.record_every) ? 0u : rec_phase[tid] + 1;
             }
         }
-        (void)any_count;
     }
     __syncthreads();
 }

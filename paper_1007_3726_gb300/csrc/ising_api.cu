@@ -163,7 +163,7 @@ void destroy_all(ising_lattice *h)
 {
     if (!h) return;
     cudaSetDevice(h->device);
-    if (h->stream || true) cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->stream);
     h->alloc.release(h->d_spins, h->stream);
     h->alloc.release(h->d_acc, h->stream);
     if (h->h_acc) cudaFreeHost(h->h_acc);

@@ -22,7 +22,11 @@
 #include "kernels.h"
 #include "sweep_device.cuh"
 
+#include <atomic>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace ising {
 
@@ -174,17 +178,21 @@ __global__ void k_recount(const Word *S, uint64_t L, unsigned long long *acc)
     block_accumulate(up, anti, acc);
 }
 
-int g_num_sms = 0;
+constexpr int kMaxDevices = 64;
 
+// SMs of the current device, queried once per device.
 int num_sms()
 {
-    if (g_num_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 1;
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int n = (dev >= 0 && dev < kMaxDevices) ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (n <= 0) {
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+        if (dev >= 0 && dev < kMaxDevices) cache[dev].store(n, std::memory_order_relaxed);
     }
-    return g_num_sms;
+    return n;
 }
 
 int grid_for(uint64_t work, int block, int per_sm)
@@ -269,9 +277,24 @@ bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 
 int half_sweep_blocks_per_sm(const LaunchConfig &c)
 {
+    // queried once per (device, kernel, block size)
+    static std::mutex mu;
+    static std::map<std::tuple<int, HalfSweepKernel, uint32_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const HalfSweepKernel k = half_sweep_kernel(c);
+    const auto key = std::make_tuple(dev, k, c.block);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel(c), (int)c.block, 0);
-    return n > 0 ? n : 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, (int)c.block, 0);
+    if (n <= 0) n = 1;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = n;
+    return n;
 }
 
 int resolve_grid(const LaunchConfig &c, uint64_t L, uint64_t rows)
