@@ -34,6 +34,7 @@ namespace {
 __global__ void __launch_bounds__(512, 3) k_half_sweep_field(const __grid_constant__ HalfSweepArgs a,
                                                           const __grid_constant__ FieldTable ft)
 {
+    dependent_launch_wait();
     __shared__ uint32_t tab[16];
     if (threadIdx.x < 16) tab[threadIdx.x] = ft.thr[threadIdx.x];
     __syncthreads();
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(512, 3) k_half_sweep_field(const __grid_consta
             ++rb;
         }
     }
+    dependent_launch_trigger();
     if (a.acc) block_accumulate(cnt_up, cnt_anti, a.acc);
 }
 
@@ -117,24 +119,42 @@ cudaError_t launch_half_sweep_field(HalfSweepArgs a, const FieldTable &ft, cudaS
     a.words_per_row = (uint32_t)(a.L / 32);
     a.rows_per_item = 8;  // L is a multiple of 64
     a.zero = 0u;
-    // resident blocks of the device, queried once per device
-    static std::atomic<int> resident[kMaxDevices];
+    // SMs and resident blocks per SM of the device, queried once per device
+    static std::atomic<int> sms_of[kMaxDevices], per_sm_of[kMaxDevices];
     int dev = 0;
     cudaGetDevice(&dev);
-    int cap = (dev >= 0 && dev < kMaxDevices) ? resident[dev].load(std::memory_order_relaxed) : 0;
-    if (cap <= 0) {
-        int sms = 0, per_sm = 0;
+    const bool cached = dev >= 0 && dev < kMaxDevices;
+    int sms = cached ? sms_of[dev].load(std::memory_order_relaxed) : 0;
+    int per_sm = cached ? per_sm_of[dev].load(std::memory_order_relaxed) : 0;
+    if (sms <= 0 || per_sm <= 0) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_half_sweep_field, kFieldBlock, 0);
-        cap = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-        if (dev >= 0 && dev < kMaxDevices) resident[dev].store(cap, std::memory_order_relaxed);
+        if (sms <= 0) sms = 1;
+        if (per_sm <= 0) per_sm = 1;
+        if (cached) {
+            sms_of[dev].store(sms, std::memory_order_relaxed);
+            per_sm_of[dev].store(per_sm, std::memory_order_relaxed);
+        }
     }
+    const int cap = sms * per_sm;
     const uint64_t items = (a.L / 8) * (uint64_t)a.words_per_row;
     const uint64_t need = (items + kFieldBlock - 1) / kFieldBlock;
     const int grid = (int)(need < (uint64_t)cap ? need : (uint64_t)cap);
     prepare_half_sweep(a, grid, kFieldBlock);
-    k_half_sweep_field<<<grid, kFieldBlock, 0, s>>>(a, ft);
-    return cudaGetLastError();
+    // programmatic stream serialization, as the zero-field step kernels, except for
+    // grids between half and twice the SM count, where it measured slower
+    // (L = 4096: 440 against 510 attempts/ns)
+    const bool dependent = grid < sms / 2 || grid >= 2 * sms;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)kFieldBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = dependent ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_half_sweep_field, a, ft);
 }
 
 }  // namespace ising

@@ -41,6 +41,7 @@ namespace {
 template <typename Word, int INS>
 __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
 {
+    dependent_launch_wait();
     constexpr int NB = WordTraits<Word>::bits / 8;  // Philox calls (bytes) per word
     Word *const S = static_cast<Word *>(a.spins);
     const uint64_t rows = a.rows;
@@ -84,6 +85,7 @@ __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
             ++rb;
         }
     }
+    dependent_launch_trigger();
     if (a.acc) block_accumulate(cnt_up, cnt_anti, a.acc);
 }
 
@@ -245,6 +247,22 @@ uint64_t mulA(uint32_t x) { return (uint64_t)x * kPhiloxMulA; }
 uint64_t mulB(uint32_t x) { return (uint64_t)x * kPhiloxMulB; }
 }  // namespace
 
+cudaError_t launch_dependent(void (*kernel)(HalfSweepArgs), int grid, int block, cudaStream_t s,
+                             const HalfSweepArgs &a)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 void prepare_half_sweep(HalfSweepArgs &a, int grid, int block)
 {
     const uint64_t pb = mulB(a.t);
@@ -320,8 +338,7 @@ cudaError_t launch_half_sweep(HalfSweepArgs a, const LaunchConfig &c, cudaStream
     a.rows_per_item = c.rows_per_item;
     a.zero = 0u;
     prepare_half_sweep(a, grid, (int)c.block);
-    half_sweep_kernel(c)<<<grid, c.block, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(half_sweep_kernel(c), grid, (int)c.block, s, a);
 }
 
 cudaError_t launch_init_hot(void *spins, uint64_t L, uint32_t word_bits, uint64_t seed,

@@ -52,6 +52,12 @@ struct HalfSweepArgs {
 // Fills the step-uniform Philox values and the grid-stride constants.
 void prepare_half_sweep(HalfSweepArgs &a, int grid, int block);
 
+// Launches a step kernel with programmatic stream serialization: its grid may be
+// scheduled while the previous kernel of the stream drains; the kernel waits
+// (griddepcontrol.wait) before it reads the lattice.
+cudaError_t launch_dependent(void (*kernel)(HalfSweepArgs), int grid, int block, cudaStream_t s,
+                             const HalfSweepArgs &a);
+
 // A launch configuration of the half-sweep.  Every valid configuration gives
 // bit-identical results; they differ only in speed.  proc_bits == 8 selects the
 // one-CTA kernel of tiny.cu instead (whole lattice in shared memory, every

@@ -42,6 +42,20 @@ __device__ __forceinline__ void philox_rounds(uint32_t &x0, uint32_t &x1, uint32
     philox_rounds_from<0>(x0, x1, x2, x3, k);
 }
 
+// Programmatic dependent launch: the step kernels are launched so that the next
+// step's grid may be scheduled while this one drains.  Before a kernel touches
+// global memory it waits until the grid before it has completed and its writes
+// are visible; when a block has finished its items it lets the dependents
+// launch (both are no-ops for a launch without the attribute).
+__device__ __forceinline__ void dependent_launch_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void dependent_launch_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename Word>
 struct WordTraits;
 template <>
@@ -230,13 +244,14 @@ __device__ __forceinline__ Word update_word(const HalfSweepArgs &a, Word cur, Wo
     const Word p4 = Tr::from_halves(h4) << off;
     const Word p8 = Tr::from_halves(h8) << off;
     Word sel = mask;
-    if (NQ < NB) sel &= (((Word)1 << (8 * NQ)) - 1) << (8 * q0);  // this thread's bytes
+    if constexpr (NQ < NB) sel &= (((Word)1 << (8 * NQ)) - 1) << (8 * q0);  // this thread's bytes
     const Word flip = sel & (ge2 | (eq1 & p4) | (eq0 & p8));
     const Word nw = cur ^ flip;
     if (count) {
         // after the step: +1 spins of the word, and the anti-aligned bonds of
         // its target sites (their neighbours are final)
-        const Word own = (NQ < NB) ? ((((Word)1 << (8 * NQ)) - 1) << (8 * q0)) : ~(Word)0;
+        Word own = ~(Word)0;
+        if constexpr (NQ < NB) own = (((Word)1 << (8 * NQ)) - 1) << (8 * q0);
         cnt_up += Tr::popc(nw & own);
         cnt_anti += Tr::popc(sel & (nw ^ up)) + Tr::popc(sel & (nw ^ dn)) +
                     Tr::popc(sel & (nw ^ left)) + Tr::popc(sel & (nw ^ right));
