@@ -146,8 +146,8 @@ ISING_API ising_status ising_field_thresholds(double T, double H, uint32_t thr[1
 /*
  * Change the temperature / the field of a lattice from its next sweep on
  * (annealing, field sweeps).  Sweeps already queued keep the old values.  The
- * moments of ising_measure use the current T.  Lattices in a nonzero field run
- * through ising_sweep only (the batch and the server reject them).
+ * moments of ising_measure use the current T.  A batch keeps the values the
+ * lattices had when it was created.
  */
 ISING_API ising_status ising_set_temperature(ising_lattice *h, double T);
 ISING_API ising_status ising_set_field(ising_lattice *h, double H);
@@ -287,9 +287,9 @@ typedef struct {
 /* Plans a batch of n distinct handles on one device; each run advances handle
  * i by nsweeps[i] sweeps (1 .. 2^30) and records samples every record_every
  * sweeps as ising_sweep does.  ISING_ERR_INVALID if the lattices do not fit in
- * the GPU's shared memory at once, or if one is in a nonzero field.  The batch
- * takes each lattice's temperature when it is created.  The handles must
- * outlive the batch. */
+ * the GPU's shared memory at once.  The batch takes each lattice's temperature
+ * and field when it is created (lattices in a field use the ten-class update of
+ * ising_field_thresholds).  The handles must outlive the batch. */
 ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, const uint64_t *nsweeps,
                                           uint32_t record_every, const ising_batch_opts *opts,
                                           ising_batch **out);

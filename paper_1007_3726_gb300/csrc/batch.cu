@@ -14,6 +14,7 @@
 // the same device code as the one-lattice kernel, so every lattice, sample and
 // final state is bit-identical to ising_sweep's.
 #include "batch_internal.h"
+#include "field_device.cuh"
 #include "handle.h"
 #include "kernels.h"
 #include "runtime.h"
@@ -48,6 +49,8 @@ struct BatchStrip {
     uint32_t thr4, thr8, c3base;        // thresholds, stream_id << 1
     const unsigned int *up_progress, *dn_progress;  // the neighbouring strips' progress
     const uint64_t *up_border, *dn_border;          // and border arrays
+    const uint32_t *field_tab;          // in a field: the lattice's 16 class thresholds (else null)
+    uint32_t k_up, k_dn;                // and its always-accepted classes (field.h)
     RoundKeys key;
 };
 
@@ -121,6 +124,29 @@ __device__ __forceinline__ void strip_step_args(HalfSweepArgs &a, const BatchStr
 
 constexpr uint32_t kMaxStripsPerCta = 64;
 
+// INS = kFieldIns: the kernel of batches that hold a lattice in a field.  It
+// picks the ten-class field update for the strips of such lattices (class
+// table read through the read-only cache) and the plain update for the others.
+// A separate kernel, so that the field code costs the other batches nothing.
+constexpr int kFieldIns = 3;
+
+// The new value of one word (or of this thread's bytes of it) of a strip.
+template <int INS, int NQ>
+__device__ __forceinline__ uint64_t batch_word(const BatchStrip &st, const HalfSweepArgs &a, uint64_t cur,
+                                               uint64_t up, uint64_t dn, uint64_t lw, uint64_t rw, uint32_t off,
+                                               uint64_t g, bool count, unsigned int &cu, unsigned int &ca,
+                                               uint32_t sub)
+{
+    if constexpr (INS == kFieldIns) {
+        if (st.field_tab)
+            return update_word_field<uint64_t, NQ, true>(a, st.field_tab, st.k_up, st.k_dn, cur, up, dn, lw, rw,
+                                                         off, g, count, cu, ca, sub * NQ);
+        return update_word<uint64_t, 0, NQ>(a, cur, up, dn, lw, rw, off, g, count, cu, ca, sub * NQ);
+    } else {
+        return update_word<uint64_t, INS, NQ>(a, cur, up, dn, lw, rw, off, g, count, cu, ca, sub * NQ);
+    }
+}
+
 // One item of a strip: R rows of one word column, or of one NQ-byte part of it
 // when 8 / NQ threads share the word (each writes only its own bytes).
 template <int INS, int NQ>
@@ -148,8 +174,7 @@ __device__ __forceinline__ void batch_item(const BatchStrip &st, const HalfSweep
     uint32_t off = (uint32_t)((y0 + p) & 1u);
     for (uint32_t r = r0; r < r1; ++r) {
         const uint64_t dn = row[W + w];
-        const uint64_t nw = update_word<uint64_t, INS, NQ>(a, cur, up, dn, row[wl], row[wr], off, g,
-                                                           count, cu, ca, sub * NQ);
+        const uint64_t nw = batch_word<INS, NQ>(st, a, cur, up, dn, row[wl], row[wr], off, g, count, cu, ca, sub);
         if (NQ == 8) {
             row[w] = nw;
         } else if (NQ == 4) {
@@ -196,8 +221,7 @@ __device__ __forceinline__ void whole_item(const BatchStrip &st, const HalfSweep
     for (uint32_t r = r0; r < r1; ++r) {
         const uint64_t *dnrow = (r + 1 == nrows) ? base : row + W;
         const uint64_t dn = dnrow[w];
-        const uint64_t nw = update_word<uint64_t, INS, NQ>(a, cur, up, dn, row[wl], row[wr], off, g, count, cu,
-                                                           ca, sub * NQ);
+        const uint64_t nw = batch_word<INS, NQ>(st, a, cur, up, dn, row[wl], row[wr], off, g, count, cu, ca, sub);
         if (NQ == 8) {
             row[w] = nw;
         } else if (NQ == 4) {
@@ -515,8 +539,9 @@ __global__ void __launch_bounds__(512, 2) k_batch(const __grid_constant__ BatchL
 namespace {
 using namespace ising;
 using BatchKernel = void (*)(BatchLaunchArgs);
-BatchKernel batch_kernel(uint32_t insert)
+BatchKernel batch_kernel(uint32_t insert, bool field)
 {
+    if (field) return k_batch<kFieldIns>;
     if (insert == 1) return k_batch<1>;
     if (insert == 2) return k_batch<2>;
     return k_batch<0>;
@@ -572,7 +597,7 @@ void plan_budget(const ising_batch *b, uint32_t *P_out, size_t *smem_cta_out)
     {
         // no more CTAs per SM than the registers allow
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->opts.insert), (int)block, 0) ==
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel(b->opts.insert, b->field), (int)block, 0) ==
                 cudaSuccess &&
             occ > 0)
             ctas_per_sm = std::min<uint32_t>(ctas_per_sm, (uint32_t)occ);
@@ -580,7 +605,7 @@ void plan_budget(const ising_batch *b, uint32_t *P_out, size_t *smem_cta_out)
     // dynamic shared memory per CTA: the SM's share, less the kernel's static
     // tables and the 1 KiB the runtime reserves per block
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, (const void *)batch_kernel(b->opts.insert));
+    cudaFuncGetAttributes(&fa, (const void *)batch_kernel(b->opts.insert, b->field));
     const size_t reserve = fa.sharedSizeBytes + 1024;
     size_t smem_cta = (size_t)smem_sm / ctas_per_sm;
     smem_cta = smem_cta > reserve ? smem_cta - reserve : 0;
@@ -766,6 +791,9 @@ ising_status alloc_batch(ising_batch *b)
     off = (off + 15) & ~(size_t)15;
     b->off_t0 = off;
     off += n * 4;
+    off = (off + 15) & ~(size_t)15;
+    const size_t off_field = off;  // 16 class thresholds per lattice (used by lattices in a field)
+    off += n * 64;
     b->plan_bytes = (off + 255) & ~(size_t)255;
     // work block: borders | progress | counters | error
     size_t w = 0;
@@ -835,6 +863,11 @@ ising_status alloc_batch(ising_batch *b)
         st.samples = reinterpret_cast<unsigned long long *>(work + b->off_counters) +
                      2 * b->sample_base[st.lat_index];
         st.final_counts = st.samples + 2 * b->nrec[st.lat_index];
+        st.field_tab = h->H != 0.0 ? reinterpret_cast<const uint32_t *>(static_cast<char *>(b->d_plan) + off_field) +
+                                         16 * st.lat_index
+                                   : nullptr;
+        st.k_up = h->field.k_up;
+        st.k_dn = h->field.k_dn;
     }
     for (size_t i = 0; i < ns; ++i) {
         BatchStrip &st = b->strips[i];
@@ -847,6 +880,8 @@ ising_status alloc_batch(ising_batch *b)
     std::memcpy(host.data() + off_strips, b->strips.data(), ns * sizeof(BatchStrip));
     std::memcpy(host.data() + off_first, b->cta_first.data(), b->cta_first.size() * 4);
     std::memcpy(host.data() + off_cstr, b->cta_strips.data(), b->cta_strips.size() * 4);
+    for (size_t i = 0; i < n; ++i)
+        std::memcpy(host.data() + off_field + 64 * i, b->hs[i]->field.thr, 64);
     cudaError_t e = cudaMemcpyAsync(b->d_plan, host.data(), b->plan_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, e, "batch plan upload");
@@ -866,12 +901,12 @@ ising_status alloc_batch(ising_batch *b)
     cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->device);
     b->args.wait_cycles = (long long)(ms * (clk_khz > 0 ? clk_khz : 2000000));
     b->args.hold_strip = b->opts.hold_strip;
-    e = cudaFuncSetAttribute(batch_kernel(b->opts.insert), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(batch_kernel(b->opts.insert, b->field), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)b->smem_bytes);
     if (e != cudaSuccess) return bfail(b, e, "batch shared memory");
     // every CTA must be resident at once
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->opts.insert), (int)b->block,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->opts.insert, b->field), (int)b->block,
                                                       b->smem_bytes);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -904,7 +939,7 @@ cudaError_t enqueue_run(ising_batch *b)
     cfg.stream = b->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelExC(&cfg, (const void *)batch_kernel(b->opts.insert), params);
+    e = cudaLaunchKernelExC(&cfg, (const void *)batch_kernel(b->opts.insert, b->field), params);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->h_counters, work + b->off_counters, b->slots * 16, cudaMemcpyDeviceToHost,
                             b->stream);
@@ -972,6 +1007,7 @@ ising_status batch_replan(ising_batch *b, const std::vector<ising_lattice *> &hs
     b->hs = hs;
     b->sweeps = sweeps;
     b->record_every = record_every;
+    b->field = std::any_of(hs.begin(), hs.end(), [](const ising_lattice *h) { return h->H != 0.0; });
     ising_status st = make_plan(b);
     if (st == ISING_OK) st = alloc_batch(b);
     if (st != ISING_OK) b->hs.clear();
@@ -1005,8 +1041,6 @@ ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, 
         if (st != ISING_OK) return st;
         for (uint32_t k = 0; k < i; ++k)
             if (hs[k] == hs[i]) return fail(ISING_ERR_INVALID, "a handle appears twice");
-        if (hs[i]->H != 0.0)
-            return fail(ISING_ERR_INVALID, "lattice %u is in a nonzero field; it runs through ising_sweep", i);
     }
     ising_batch *b = nullptr;
     ising_status st = batch_new(hs[0]->device, opts, &b);

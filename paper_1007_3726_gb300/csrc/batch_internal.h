@@ -58,6 +58,7 @@ struct ising_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     ising::BatchLaunchArgs args{};
+    bool field = false;                     // a lattice is in a field: the field kernel
     bool failed = false;
 };
 

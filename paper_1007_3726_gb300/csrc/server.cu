@@ -352,7 +352,6 @@ ISING_API ising_status ising_server_submit(ising_server *s, const ising_request 
     uint32_t wb = 0;
     ising_status st = validate_params(&req->params, &wb);
     if (st != ISING_OK) return st;
-    if (req->params.H != 0.0) return fail(ISING_ERR_INVALID, "served lattices have H = 0");
     if (req->nsweeps == 0 || req->nsweeps >= 0xFFFFFFFFull)
         return fail(ISING_ERR_INVALID, "nsweeps must be in [1, 2^32 - 1)");
     Request *r = new (std::nothrow) Request();

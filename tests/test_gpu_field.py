@@ -143,27 +143,60 @@ def test_field_split_calls_and_checkpoint(P, orc, tmp_path):
     b.close()
 
 
-def test_batch_and_server_reject_a_field(P):
-    with P.Lattice(128, 2.0, H=0.5) as lat:
-        with pytest.raises(P.IsingError) as ei:
-            P.ising_sweep_batch([lat], [10], 1)
-        assert ei.value.status == P.ERR_INVALID
-        assert "field" in str(ei.value)
-    lat0 = P.Lattice(128, 2.0)
-    lat0.set_field(0.3)
-    with pytest.raises(P.IsingError):
-        P.ising_sweep_batch([lat0], [10], 1)
-    lat0.set_field(0.0)
-    P.ising_sweep_batch([lat0], [10], 1)  # back to zero field: accepted
-    lat0.close()
-    srv = P.Server(hbm_budget_bytes=1 << 28)
-    try:
-        with pytest.raises(P.IsingError) as ei:
-            srv.submit(128, 2.0, 100, H=0.5)
-        assert ei.value.status == P.ERR_INVALID
-        srv.submit(128, 2.0, 10, H=0.0)
-    finally:
-        srv.close()
+def test_batch_in_a_field_bit_exact(P, orc):
+    """A persistent batch that mixes lattices in a field with zero-field ones, one
+    of them over several CTAs with border exchange (L = 2048), against the
+    oracle's field update lattice by lattice."""
+    specs = [(64, 2.0, 0.3), (128, 2.4, 0.0), (256, 1.8, -1.0), (512, 3.0, 2.5), (2048, 2.269185, 0.1)]
+    n, re = 6, 2
+    lats = [P.Lattice(L, T, seed=40 + i, stream_id=i, init="hot", H=H) for i, (L, T, H) in enumerate(specs)]
+    with P.Batch(lats, [n] * len(lats), re) as b:
+        assert b.info()["strips"] > len(lats)  # the L = 2048 lattice is split into strips
+        b.run(1)
+    for i, ((L, T, H), lat) in enumerate(zip(specs, lats)):
+        s = orc.init_hot(L, 40 + i, i)
+        if H == 0.0:
+            thr4, thr8 = orc.thresholds(T)
+            Mo, Eo = orc.run(s, n, 40 + i, i, thr4, thr8)
+        else:
+            Mo, Eo = orc.run_field(s, n, 40 + i, i, T, H)
+        M, E = lat.samples()
+        assert np.array_equal(M, Mo[re - 1::re]) and np.array_equal(E, Eo[re - 1::re]), (L, H)
+        assert np.array_equal(lat.spins(), s), (L, H)
+        lat.close()
+
+
+def test_server_in_a_field_equals_alone(P):
+    """Served requests in a field give the same samples as the same lattice run alone."""
+    reqs = [dict(L=64, T=2.0, H=0.4, n=30), dict(L=256, T=2.5, H=-0.2, n=20), dict(L=128, T=1.5, H=0.0, n=25),
+            dict(L=512, T=3.0, H=1.7, n=12)]
+    with P.Server(hbm_budget_bytes=1 << 26, epoch_sweeps=7, keep_samples=True) as srv:
+        ids = [srv.submit(r["L"], r["T"], r["n"], seed=100 + i, record_every=1, tag=i, H=r["H"])
+               for i, r in enumerate(reqs)]
+        got = {}
+        while len(got) < len(reqs):
+            for res in srv.poll(wait_s=1.0):
+                got[res["tag"]] = res
+        for i, r in enumerate(reqs):
+            assert got[i]["status"] == P.OK
+            M, E = srv.samples(ids[i])
+            with P.Lattice(r["L"], r["T"], seed=100 + i, init="hot", H=r["H"]) as lat:
+                Ma, Ea = lat.sweep(r["n"], 1, collect=True)
+            assert np.array_equal(M, Ma) and np.array_equal(E, Ea), r
+
+
+def test_batch_keeps_the_field_it_was_made_with(P, orc):
+    """A batch takes each lattice's field when it is made; set_field afterwards
+    changes ising_sweep, not the batch's runs."""
+    L, T = 128, 2.2
+    lat = P.Lattice(L, T, seed=3, init="hot", H=0.5)
+    with P.Batch([lat], [4], 1) as b:
+        lat.set_field(0.0)
+        b.run(1)
+    s = orc.init_hot(L, 3, 0)
+    orc.run_field(s, 4, 3, 0, T, 0.5)
+    assert np.array_equal(lat.spins(), s)
+    lat.close()
 
 
 def test_set_temperature_validates(P):
