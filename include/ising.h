@@ -224,7 +224,7 @@ ISING_API const char *ising_last_error(void);
  * memory and every sweep of an ising_sweep call runs in one launch, with a
  * block barrier as the synchronisation between steps A and B.  Then block is
  * its size, rows_per_item the threads that share one 32-bit word (1, 2 or 4),
- * regcap = insert = 0 and grid = 1.  It is the default for L <= 256.  In a
+ * regcap = insert = 0 and grid = 1.  It is the default for L <= 128.  In a
  * field (H != 0) it uses one thread per word whatever rows_per_item says; the
  * step kernels are then replaced by the field step kernel.
  */

@@ -41,11 +41,13 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
         auto it = g_tuned.find(std::make_tuple(device, L, word_bits));
         if (it != g_tuned.end()) return it->second;
     }
-    // one CTA for small lattices (the fastest shapes measured at L = 64, 128, 256)
-    if (L <= 256 && tiny_lattice_ok(L))
+    // untuned: the shapes the autotuner picked on GB300 at these sizes
+    // (fields: proc_bits, regcap, insert, block, rows_per_item, grid)
+    if (L <= 128 && tiny_lattice_ok(L))  // one CTA, every sweep of a call in one launch
         return L == 64 ? LaunchConfig{kTinyProcBits, 0, 0, 256, 2, 1} : LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 1};
-    LaunchConfig c{64, 1, 1, 512, 8, 0};
-    return c;
+    if (L < 4096) return LaunchConfig{32, 1, 0, 256, 2, 0};
+    if (L < 16384) return LaunchConfig{64, 1, 0, 512, 4, 0};
+    return LaunchConfig{64, 1, 0, 512, 8, 0};
 }
 
 void remember_launch(int device, uint64_t L, uint32_t word_bits, const LaunchConfig &c)

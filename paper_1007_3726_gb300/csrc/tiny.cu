@@ -134,7 +134,7 @@ bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 LaunchConfig plain_launch(const LaunchConfig &c)
 {
     if (c.proc_bits == 32 || c.proc_bits == 64) return c;
-    return LaunchConfig{64, 1, 1, 512, 8, 0};
+    return LaunchConfig{32, 1, 0, 256, 2, 0};  // the step shape of small lattices
 }
 
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, cudaStream_t s)
