@@ -46,7 +46,7 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
     if (L <= 128 && tiny_lattice_ok(L))  // one CTA, every sweep of a call in one launch
         return L == 64 ? LaunchConfig{kTinyProcBits, 0, 0, 256, 2, 1} : LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 1};
     if (L < 4096) return LaunchConfig{32, 1, 0, 256, 2, 0};
-    if (L < 16384) return LaunchConfig{64, 1, 0, 512, 4, 0};
+    if (L < 16384) return LaunchConfig{64, 0, 0, 512, 4, 0};
     return LaunchConfig{64, 1, 0, 512, 8, 0};
 }
 
