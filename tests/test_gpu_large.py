@@ -54,3 +54,30 @@ def test_largest_lattice_L524288(P, orc):
     assert abs(m.mean() - exact.onsager_m0(T)) < 1e-3, m.mean()
     # the energy per spin approaches Onsager's u(T) as well (finite time, looser)
     assert abs(E[-1] / N - exact.onsager_u(T)) < 5e-3
+
+
+def test_maximum_lattice_L1048576(P, orc):
+    """The ABI's largest lattice, L = 2^20 (2^40 spins, 128 GiB in 64-bit words), from a
+    hot start: the hot start's counter word 1 (n >> 39) and the sweep's group
+    indices up to 2^37 are in use.  Rows of three windows (the wrap-around, the
+    first row of the upper half, the last rows) after 2 sweeps against the
+    oracle's hot start and light-cone evolution of the same rows; the fused
+    M/E against a GPU recount."""
+    import torch
+
+    free, _ = torch.cuda.mem_get_info()
+    if free < 140 * 2 ** 30:
+        pytest.skip("needs 140 GiB of free device memory")
+    L, T, seed, k = 2 ** 20, 2.269185, 9, 2
+    thr4, thr8 = orc.thresholds(T)
+    lat = P.Lattice(L, T, seed=seed, stream_id=1, init="hot", word_bits=64)
+    M, E = lat.sweep(k, 1, collect=True)
+    margin = 2 * k + 1
+    for row0 in (L - 3, L // 2, L - 40):
+        nrows = 32
+        first = (row0 - margin) % L
+        w = orc.init_hot(L, seed, 1, row0=first, nrows=nrows + 2 * margin)
+        orc.run_window(w, L, first, k, seed, 1, thr4, thr8)
+        assert np.array_equal(lat.spins(row0, nrows), w[margin:margin + nrows]), row0  # rows wrap
+    assert (int(M[-1]), int(E[-1])) == lat.recount()
+    lat.close()
