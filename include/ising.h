@@ -227,9 +227,17 @@ ISING_API const char *ising_last_error(void);
  * regcap = insert = 0 and grid = 1.  It is the default for L <= 128.  In a
  * field (H != 0) it uses one thread per word whatever rows_per_item says; the
  * step kernels are then replaced by the field step kernel.
+ * persistent = 1 (with proc_bits 32 or 64, insert 0, grid 0; regcap 0, 1 or
+ * 2 = the compiler's choice, <= 40 or <= 64 registers)
+ * runs every sweep of an ising_sweep call in one cooperative launch of that
+ * step shape, all blocks resident, with a grid-wide barrier between steps A
+ * and B instead of a kernel boundary; for lattices the autotuner's scratch holds
+ * whole (L <= 65536).  In a field the field step kernel runs instead.
+ * persistent = 0 otherwise.
  */
 typedef struct {
     uint32_t proc_bits, regcap, block, rows_per_item, grid, insert;
+    uint32_t persistent;
 } ising_launch;
 
 /* The handle's current configuration. */

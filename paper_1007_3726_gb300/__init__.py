@@ -61,7 +61,7 @@ class IsingObs(ctypes.Structure):
 class IsingLaunch(ctypes.Structure):
     _fields_ = [("proc_bits", ctypes.c_uint32), ("regcap", ctypes.c_uint32), ("block", ctypes.c_uint32),
                 ("rows_per_item", ctypes.c_uint32), ("grid", ctypes.c_uint32),
-                ("insert", ctypes.c_uint32)]
+                ("insert", ctypes.c_uint32), ("persistent", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

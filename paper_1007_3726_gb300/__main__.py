@@ -55,7 +55,7 @@ def main(argv=None):
     ap.add_argument("--time", action="store_true", help="report wall time of the sweeps")
     ap.add_argument("--autotune", action="store_true", help="pick the launch configuration first")
     ap.add_argument("--launch", default=None,
-                    help="launch configuration proc_bits,regcap,block,rows_per_item[,grid[,insert]]")
+                    help="launch configuration proc_bits,regcap,block,rows_per_item[,grid[,insert[,persistent]]]")
     a = ap.parse_args(argv)
 
     import paper_1007_3726_gb300 as P
@@ -67,7 +67,7 @@ def main(argv=None):
         cfg, _ = lat.autotune()
     if a.launch:
         v = [int(x) for x in a.launch.split(",")]
-        keys = ["proc_bits", "regcap", "block", "rows_per_item", "grid", "insert"]
+        keys = ["proc_bits", "regcap", "block", "rows_per_item", "grid", "insert", "persistent"]
         lat.set_launch(**dict(zip(keys, v)))
     t0 = time.perf_counter()
     lat.sweep(a.sweeps, a.record_every)

@@ -24,11 +24,11 @@ std::map<std::tuple<int, uint64_t, uint32_t>, LaunchConfig> g_tuned;
 
 ising_launch to_abi(const LaunchConfig &c)
 {
-    return ising_launch{c.proc_bits, c.regcap, c.block, c.rows_per_item, c.grid, c.insert};
+    return ising_launch{c.proc_bits, c.regcap, c.block, c.rows_per_item, c.grid, c.insert, c.persistent};
 }
 LaunchConfig from_abi(const ising_launch &l)
 {
-    return LaunchConfig{l.proc_bits, l.regcap, l.insert, l.block, l.rows_per_item, l.grid};
+    return LaunchConfig{l.proc_bits, l.regcap, l.insert, l.block, l.rows_per_item, l.grid, l.persistent};
 }
 }  // namespace
 
@@ -73,6 +73,15 @@ std::vector<LaunchConfig> launch_candidates(uint64_t L, uint64_t rows)
                         LaunchConfig c{pb, rc, ins, blk, R, 0};
                         if (launch_config_valid(c, L, rows)) out.push_back(c);
                     }
+    // every sweep of a call in one cooperative launch, for the step shapes that
+    // suit the lattices whose steps are short
+    for (uint32_t pb : {32u, 64u})
+        for (uint32_t rc : {0u, 1u, 2u})
+            for (uint32_t blk : {256u, 512u})
+                for (uint32_t R : {2u, 4u, 8u}) {
+                    LaunchConfig c{pb, rc, 0, blk, R, 0, 1};
+                    if (launch_config_valid(c, L, rows)) out.push_back(c);
+                }
     // larger grids than the resident one (the block scheduler evens out the tail):
     // for the shapes that use all registers of the 40-register cap
     for (uint32_t pb : {32u, 64u})
@@ -161,7 +170,25 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
     for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
         const LaunchConfig &c = cands[i];
         uint32_t steps = 2 * reps;
-        if (c.proc_bits == kTinyProcBits) {
+        if (c.persistent) {
+            // one launch runs many sweeps: time one of 8 reps sweeps after a 1-sweep launch
+            HalfSweepArgs pa{};
+            pa.spins = scratch;
+            pa.L = h->L;
+            pa.key = h->key;
+            pa.thr4 = h->thr4;
+            pa.thr8 = h->thr8;
+            SweepsRun sr{};
+            sr.t0 = 0xFFFFF000u;  // any value: the scratch is thrown away
+            sr.nsweeps = 1;
+            sr.c3base = h->stream_id << 1;
+            sr.acc = h->d_acc;
+            e = launch_sweeps(pa, c, sr, h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            sr.nsweeps = 8 * reps;
+            if (e == cudaSuccess) e = launch_sweeps(pa, c, sr, h->stream);
+            steps = 16 * reps;
+        } else if (c.proc_bits == kTinyProcBits) {
             // one launch runs many sweeps: time one of 8 reps sweeps after a 1-sweep warm-up
             TinyRunArgs ta{};
             ta.spins = scratch;
@@ -181,7 +208,7 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
             if (e == cudaSuccess) e = launch_tiny(ta, c.block, c.rows_per_item, h->stream);
             steps = 16 * reps;
         }
-        for (uint32_t r = 0; r <= reps && e == cudaSuccess && c.proc_bits != kTinyProcBits; ++r) {
+        for (uint32_t r = 0; r <= reps && e == cudaSuccess && c.proc_bits != kTinyProcBits && !c.persistent; ++r) {
             if (r == 1) e = cudaEventRecord(e0, h->stream);
             for (uint32_t p = 0; p < 2 && e == cudaSuccess; ++p) {
                 a.p = p;
@@ -196,9 +223,9 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         const double step_ms = (double)ms / steps;
         if (e == cudaSuccess && log)
-            std::fprintf(stderr, "autotune L=%llu rows=%llu proc_bits=%u regcap=%u insert=%u block=%u R=%u grid=%u: %.2f us/step\n",
+            std::fprintf(stderr, "autotune L=%llu rows=%llu proc_bits=%u regcap=%u insert=%u block=%u R=%u grid=%u persistent=%u: %.2f us/step\n",
                          (unsigned long long)h->L, (unsigned long long)rows, c.proc_bits, c.regcap,
-                         c.insert, c.block, c.rows_per_item, c.grid, 1e3 * step_ms);
+                         c.insert, c.block, c.rows_per_item, c.grid, c.persistent, 1e3 * step_ms);
         if (e == cudaSuccess && step_ms < best_step_ms) {
             best_step_ms = step_ms;
             best_c = c;

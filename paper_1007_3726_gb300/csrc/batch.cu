@@ -139,11 +139,11 @@ __device__ __forceinline__ uint64_t batch_word(const BatchStrip &st, const HalfS
 {
     if constexpr (INS == kFieldIns) {
         if (st.field_tab)
-            return update_word_field<uint64_t, NQ, true>(a, st.field_tab, st.k_up, st.k_dn, cur, up, dn, lw, rw,
+            return update_word_field<uint64_t, NQ, true>(a, a, st.field_tab, st.k_up, st.k_dn, cur, up, dn, lw, rw,
                                                          off, g, count, cu, ca, sub * NQ);
-        return update_word<uint64_t, 0, NQ>(a, cur, up, dn, lw, rw, off, g, count, cu, ca, sub * NQ);
+        return update_word<uint64_t, 0, NQ>(a, a, cur, up, dn, lw, rw, off, g, count, cu, ca, sub * NQ);
     } else {
-        return update_word<uint64_t, INS, NQ>(a, cur, up, dn, lw, rw, off, g, count, cu, ca, sub * NQ);
+        return update_word<uint64_t, INS, NQ>(a, a, cur, up, dn, lw, rw, off, g, count, cu, ca, sub * NQ);
     }
 }
 

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(512, 3) k_half_sweep_field(const __grid_consta
         for (uint32_t r = 0; r < R; ++r) {
             uint32_t *const pn = (y0 + r + 1 == rows) ? S + w : p + W;
             const uint32_t dn = *pn;
-            const uint32_t nw = update_word_field(a, tab, ft.k_up, ft.k_dn, cur, up, dn, p[dl], p[dr], off, g,
+            const uint32_t nw = update_word_field(a, a, tab, ft.k_up, ft.k_dn, cur, up, dn, p[dl], p[dr], off, g,
                                                   a.acc != nullptr, cnt_up, cnt_anti);
             *p = nw;
             up = nw;

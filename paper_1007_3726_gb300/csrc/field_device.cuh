@@ -24,8 +24,8 @@ __device__ __forceinline__ Word count_at_least(uint32_t k, Word b0, Word b1, Wor
 // are drawn and only those bytes of the result are meaningful).  tab is the
 // 16-entry threshold table, index 8 S + c, in shared memory (LDG = false) or
 // in global memory read through the read-only cache (LDG = true).
-template <typename Word, int NQ = WordTraits<Word>::bits / 8, bool LDG = false>
-__device__ __forceinline__ Word update_word_field(const HalfSweepArgs &a, const uint32_t *tab, uint32_t k_up,
+template <typename Word, int NQ = WordTraits<Word>::bits / 8, bool LDG = false, typename K, typename S>
+__device__ __forceinline__ Word update_word_field(const K &a, const S &s, const uint32_t *tab, uint32_t k_up,
                                                   uint32_t k_dn, Word cur, Word up, Word dn, Word lw, Word rw,
                                                   uint32_t off, uint64_t g, bool count, unsigned int &cnt_up,
                                                   unsigned int &cnt_anti, uint32_t q0 = 0)
@@ -56,7 +56,7 @@ __device__ __forceinline__ Word update_word_field(const HalfSweepArgs &a, const 
     // P: bit 8q + 2l of half q / 4 is set when draw l of call q is below its
     // site's threshold (with NQ < NB: the calls of this thread, all in one
     // 32-bit half, at their offsets in it)
-    const WordDraws d = word_draws_begin(a, g);
+    const WordDraws d = word_draws_begin(a, s, g);
     constexpr int NH = (NQ == NB) ? (NB + 3) / 4 : 1;
     uint32_t P[NH];
 #pragma unroll
@@ -65,7 +65,7 @@ __device__ __forceinline__ Word update_word_field(const HalfSweepArgs &a, const 
     for (int qq = 0; qq < NQ; ++qq) {
         const uint32_t q = (NQ == NB) ? (uint32_t)qq : q0 + (uint32_t)qq;
         uint32_t u[4];
-        word_draw_call(a, d, q, u);
+        word_draw_call(a, s, d, q, u);
         const int h = (NQ == NB) ? (qq >> 2) : 0;
         const uint32_t half = (NQ == NB) ? (uint32_t)(qq >> 2) : (q >> 2);
         const uint32_t Xh = (uint32_t)(X >> (32 * half)), Yh = (uint32_t)(Y >> (32 * half));

@@ -424,6 +424,24 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
         CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->stream));
         return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
     }
+    if (h->launch.persistent && h->H == 0.0) {
+        // the whole call in one cooperative launch
+        HalfSweepArgs a{};
+        a.spins = h->d_spins;
+        a.L = h->L;
+        a.key = h->key;
+        a.thr4 = h->thr4;
+        a.thr8 = h->thr8;
+        SweepsRun sr{};
+        sr.t0 = (uint32_t)t0;
+        sr.nsweeps = (uint32_t)nsweeps;
+        sr.record_every = record_every;
+        sr.nrec = (uint32_t)nrec;
+        sr.c3base = h->stream_id << 1;
+        sr.acc = h->d_acc;
+        CK(h, launch_sweeps(a, h->launch, sr, h->stream));
+        return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
+    }
     HalfSweepArgs a{};
     a.spins = h->d_spins;
     a.L = h->L;
@@ -449,7 +467,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
             if (h->H != 0.0)
                 CK(h, launch_half_sweep_field(a, h->field, h->stream));
             else
-                CK(h, launch_half_sweep(a, h->launch, h->stream));
+                CK(h, launch_half_sweep(a, plain_launch(h->launch), h->stream));
         }
     }
     if (slot == nrec && nrec > 0 && record_every && (t0 + nsweeps) % record_every == 0) {

@@ -32,59 +32,14 @@ namespace ising {
 
 namespace {
 
-// One checkerboard step.  Work item = (block of R rows, word column w); the
-// thread walks down its column keeping the rows above / at / below in
-// registers, advancing its row pointers, group index and parity mask by
-// additions.  Rows it reads but does not own (the halo rows and the adjacent
-// words) are only used at bit positions of the other parity, which no thread
-// writes during this step.
+// One checkerboard step (the items of half_sweep_items), launched as a
+// dependent launch after the previous step.
 template <typename Word, int INS>
 __device__ __forceinline__ void half_sweep_body(const HalfSweepArgs &a)
 {
     dependent_launch_wait();
-    constexpr int NB = WordTraits<Word>::bits / 8;  // Philox calls (bytes) per word
-    Word *const S = static_cast<Word *>(a.spins);
-    const uint64_t rows = a.rows;
-    const uint32_t W = a.words_per_row;
-    const uint32_t R = a.rows_per_item;
-    const uint32_t nrb = (uint32_t)(a.update_rows / R);
-    const uint64_t groups_per_row = a.L >> 3;
-
     unsigned int cnt_up = 0, cnt_anti = 0;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t rb = tid / W;
-    uint32_t w = tid - rb * W;
-    while (rb < nrb) {
-        const int64_t dl = (w == 0) ? (int64_t)W - 1 : -1;  // to the left neighbour word
-        const int64_t dr = (w + 1 == W) ? 1 - (int64_t)W : 1;
-        const uint64_t y0 = a.first_row + (uint64_t)rb * R;   // buffer row
-        const uint64_t yg = (uint64_t)(a.y_offset + (int64_t)y0);  // global row
-        Word *p = S + y0 * W + w;
-        Word up = *((y0 == 0) ? S + (rows - 1) * W + w : p - W);
-        Word cur = *p;
-        uint64_t g = yg * groups_per_row + (uint64_t)w * NB;
-        uint32_t off = (uint32_t)((yg + a.p) & 1u);  // parity of the target bit positions
-        for (uint32_t r = 0; r < R; ++r) {
-            Word *const pn = (y0 + r + 1 == rows) ? S + w : p + W;
-            const Word dn = *pn;
-            const Word lw = p[dl];
-            const Word rw = p[dr];
-            const Word nw = update_word<Word, INS>(a, cur, up, dn, lw, rw, off, g, a.acc != nullptr,
-                                                   cnt_up, cnt_anti);
-            *p = nw;
-            up = nw;
-            cur = dn;
-            p = pn;
-            g += groups_per_row;
-            off ^= 1u;
-        }
-        rb += a.stride_rb;
-        w += a.stride_w;
-        if (w >= W) {
-            w -= W;
-            ++rb;
-        }
-    }
+    half_sweep_items<Word, INS>(a, a, cnt_up, cnt_anti);
     dependent_launch_trigger();
     if (a.acc) block_accumulate(cnt_up, cnt_anti, a.acc);
 }
@@ -279,6 +234,7 @@ void prepare_half_sweep(HalfSweepArgs &a, int grid, int block)
 
 bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
+    if (c.persistent) return persistent_config_valid(c, L, rows);
     if (c.proc_bits == kTinyProcBits) return tiny_config_valid(c, L, rows);
     if (c.proc_bits != 32 && c.proc_bits != 64) return false;
     if (c.regcap > 2) return false;
@@ -327,7 +283,7 @@ int resolve_grid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 
 cudaError_t launch_half_sweep(HalfSweepArgs a, const LaunchConfig &c, cudaStream_t s)
 {
-    if (c.proc_bits != 32 && c.proc_bits != 64) return cudaErrorInvalidValue;  // not a step kernel
+    if ((c.proc_bits != 32 && c.proc_bits != 64) || c.persistent) return cudaErrorInvalidValue;  // not a step kernel
     if (a.update_rows == 0) {  // a whole periodic lattice
         a.first_row = 0;
         a.update_rows = a.rows;

@@ -70,9 +70,26 @@ struct LaunchConfig {
     uint32_t block;          // 128, 256 or 512 threads
     uint32_t rows_per_item;  // 2 .. 64, divides L
     uint32_t grid;           // blocks (0 = all resident blocks of the device)
+    uint32_t persistent;     // 1: every sweep of a call in one cooperative launch (persistent.cu)
 };
 
 bool launch_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows);
+
+// Every sweep of a call in one cooperative launch of the step items, with a
+// grid-wide barrier between the steps (persistent.cu).  Samples as TinyRunArgs.
+struct SweepsRun {
+    uint32_t t0;              // sweep index of the first sweep
+    uint32_t nsweeps;         // >= 1
+    uint32_t record_every;    // 0: record nothing
+    uint32_t nrec;            // recorded sweeps of the call
+    uint32_t c3base;          // stream_id << 1
+    unsigned long long *acc;  // nrec + 1 slots of two counters
+};
+// A persistent configuration: a step shape (proc_bits 32 / 64, regcap 0 / 1,
+// insert 0) with persistent = 1 and grid = 0 (all resident blocks).
+bool persistent_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows);
+// a as for launch_half_sweep (spins, L, key, thr4, thr8); the geometry is filled here.
+cudaError_t launch_sweeps(HalfSweepArgs a, const LaunchConfig &c, const SweepsRun &s, cudaStream_t st);
 
 constexpr uint32_t kTinyProcBits = 8;
 // Lattices the one-CTA kernel takes: L a power of two, 64 <= L <= 1024.

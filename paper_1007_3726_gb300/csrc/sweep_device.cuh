@@ -105,6 +105,13 @@ __device__ __forceinline__ void block_accumulate(unsigned int a, unsigned int b,
     }
 }
 
+// The device functions below take two argument objects: k with the launch
+// constants (the round keys key, thr4, thr8, zero) and s with the values of the
+// step (the step-uniform Philox values r1x0 .. r2x3, the parity p, and acc, not
+// null when the step counts).  A step kernel passes its launch arguments as
+// both; the persistent kernel passes its launch arguments and the step values
+// it computes.
+//
 // The Philox4x32-10 calls of one word whose first Philox group is g0, with
 // the step-uniform parts hoisted: round 1 and the word-0/word-3 half of round 2
 // come from the step-uniform values; the round-1 products A * (g0 + q) are one
@@ -116,15 +123,16 @@ struct WordDraws {
     uint32_t r2x2k, r2x3;   // round-2 words 2 (before the XOR) and 3 for hi(g0)
 };
 
-__device__ __forceinline__ WordDraws word_draws_begin(const HalfSweepArgs &a, uint64_t g0)
+template <typename K, typename S>
+__device__ __forceinline__ WordDraws word_draws_begin(const K &k, const S &s, uint64_t g0)
 {
     WordDraws d;
     const uint32_t c1 = (uint32_t)(g0 >> 32);  // the same for all groups of a word
-    d.r2x2k = a.r2x2k;
-    d.r2x3 = a.r2x3;
+    d.r2x2k = s.r2x2k;
+    d.r2x3 = s.r2x3;
     if (c1 != 0u) {
-        const uint64_t pa = (uint64_t)(a.r1x0 ^ c1) * kPhiloxMulA;
-        d.r2x2k = (uint32_t)(pa >> 32) ^ a.key.k1[1];
+        const uint64_t pa = (uint64_t)(s.r1x0 ^ c1) * kPhiloxMulA;
+        d.r2x2k = (uint32_t)(pa >> 32) ^ k.key.k1[1];
         d.r2x3 = (uint32_t)pa;
     }
     d.pa0 = (uint64_t)(uint32_t)g0 * kPhiloxMulA;
@@ -132,20 +140,21 @@ __device__ __forceinline__ WordDraws word_draws_begin(const HalfSweepArgs &a, ui
 }
 
 // The four draws of call q of the word (counter low word g0 + q).
-__device__ __forceinline__ void word_draw_call(const HalfSweepArgs &a, const WordDraws &d, uint32_t q,
+template <typename K, typename S>
+__device__ __forceinline__ void word_draw_call(const K &k, const S &s, const WordDraws &d, uint32_t q,
                                                uint32_t (&u)[4])
 {
     // round 1: words 0, 1 are uniform (r1x0 ^ c1, lo(B t))
     const uint64_t pa = d.pa0 + (uint64_t)kPhiloxMulA * (uint64_t)q;
-    const uint32_t x2 = (uint32_t)(pa >> 32) ^ a.r1x2k;
+    const uint32_t x2 = (uint32_t)(pa >> 32) ^ s.r1x2k;
     const uint32_t x3 = (uint32_t)pa;
     // round 2: the product A * word 0 is uniform per word
     const uint64_t pb = (uint64_t)x2 * kPhiloxMulB;
-    uint32_t y0 = (uint32_t)(pb >> 32) ^ a.r2x0k;
+    uint32_t y0 = (uint32_t)(pb >> 32) ^ s.r2x0k;
     uint32_t y1 = (uint32_t)pb;
     uint32_t y2 = x3 ^ d.r2x2k;
     uint32_t y3 = d.r2x3;
-    philox_rounds_from<2>(y0, y1, y2, y3, a.key);
+    philox_rounds_from<2>(y0, y1, y2, y3, k.key);
     u[0] = y0;
     u[1] = y1;
     u[2] = y2;
@@ -155,12 +164,12 @@ __device__ __forceinline__ void word_draw_call(const HalfSweepArgs &a, const Wor
 // The acceptance masks of one word whose first Philox group is g0: bit
 // 8q + 2l of half (q / 4) is set when draw l of the word's call q is below the
 // threshold.
-template <int NB, int INS, int NQ = NB>
-__device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t g0,
+template <int NB, int INS, int NQ = NB, typename K, typename S>
+__device__ __forceinline__ void word_draw_masks(const K &a, const S &s, uint64_t g0,
                                                 uint32_t (&p4)[(NB + 3) / 4],
                                                 uint32_t (&p8)[(NB + 3) / 4], uint32_t q0 = 0)
 {
-    const WordDraws d = word_draws_begin(a, g0);
+    const WordDraws d = word_draws_begin(a, s, g0);
     // INS >= 1 (>= 2) starts the P4 (P8) mask from a zero the compiler cannot
     // see, so that its bit insertions stay ORs on the ALU pipe instead of
     // becoming additions on the pipe that also carries the Philox multiplies.
@@ -177,7 +186,7 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
     for (int qq = 0; qq < NQ; ++qq) {
         const uint32_t q = (NQ == NB) ? (uint32_t)qq : q0 + (uint32_t)qq;
         uint32_t u[4];
-        word_draw_call(a, d, q, u);
+        word_draw_call(a, s, d, q, u);
         const int h = (NQ == NB) ? (qq >> 2) : 0;
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
@@ -216,8 +225,8 @@ __device__ __forceinline__ void word_draw_masks(const HalfSweepArgs &a, uint64_t
 // With NQ < NB only the Philox calls (bytes) q0 .. q0 + NQ - 1 of the word are
 // drawn and only those bytes of the returned word (and of the counts) are
 // meaningful: several threads can then share one word.
-template <typename Word, int INS, int NQ = WordTraits<Word>::bits / 8>
-__device__ __forceinline__ Word update_word(const HalfSweepArgs &a, Word cur, Word up, Word dn,
+template <typename Word, int INS, int NQ = WordTraits<Word>::bits / 8, typename K, typename S>
+__device__ __forceinline__ Word update_word(const K &a, const S &s, Word cur, Word up, Word dn,
                                             Word lw, Word rw, uint32_t off, uint64_t g, bool count,
                                             unsigned int &cnt_up, unsigned int &cnt_anti,
                                             uint32_t q0 = 0)
@@ -240,7 +249,7 @@ __device__ __forceinline__ Word update_word(const HalfSweepArgs &a, Word cur, Wo
 
     // the sites' draws: byte q of the word holds four target sites
     uint32_t h4[(NB + 3) / 4], h8[(NB + 3) / 4];
-    word_draw_masks<NB, INS, NQ>(a, g, h4, h8, q0);
+    word_draw_masks<NB, INS, NQ>(a, s, g, h4, h8, q0);
     const Word p4 = Tr::from_halves(h4) << off;
     const Word p8 = Tr::from_halves(h8) << off;
     Word sel = mask;
@@ -257,6 +266,65 @@ __device__ __forceinline__ Word update_word(const HalfSweepArgs &a, Word cur, Wo
                     Tr::popc(sel & (nw ^ left)) + Tr::popc(sel & (nw ^ right));
     }
     return nw;
+}
+
+// The items of one checkerboard step of the step kernel's geometry and launch
+// constants (a: the lattice buffer, rows, words per row, rows per item, grid
+// stride, keys, thresholds) with the step values sa (as above: the step-uniform
+// Philox values, p the parity of the updated sites, counts taken when sa.acc
+// is not null).  Work item = (block of R rows, word column w); the
+// thread walks down its column keeping the rows above / at / below in
+// registers, advancing its row pointers, group index and parity mask by
+// additions.  Rows it reads but does not own (the halo rows and the adjacent
+// words) are only used at bit positions of the other parity, which no thread
+// writes during this step.  When counting, adds this thread's counts of the
+// new state (see update_word).
+template <typename Word, int INS, typename StepArgs>
+__device__ __forceinline__ void half_sweep_items(const HalfSweepArgs &a, const StepArgs &sa, unsigned int &cnt_up,
+                                                 unsigned int &cnt_anti)
+{
+    constexpr int NB = WordTraits<Word>::bits / 8;  // Philox calls (bytes) per word
+    Word *const S = static_cast<Word *>(a.spins);
+    const uint64_t rows = a.rows;
+    const uint32_t W = a.words_per_row;
+    const uint32_t R = a.rows_per_item;
+    const uint32_t nrb = (uint32_t)(a.update_rows / R);
+    const uint64_t groups_per_row = a.L >> 3;
+
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t rb = tid / W;
+    uint32_t w = tid - rb * W;
+    while (rb < nrb) {
+        const int64_t dl = (w == 0) ? (int64_t)W - 1 : -1;  // to the left neighbour word
+        const int64_t dr = (w + 1 == W) ? 1 - (int64_t)W : 1;
+        const uint64_t y0 = a.first_row + (uint64_t)rb * R;   // buffer row
+        const uint64_t yg = (uint64_t)(a.y_offset + (int64_t)y0);  // global row
+        Word *q = S + y0 * W + w;
+        Word up = *((y0 == 0) ? S + (rows - 1) * W + w : q - W);
+        Word cur = *q;
+        uint64_t g = yg * groups_per_row + (uint64_t)w * NB;
+        uint32_t off = (uint32_t)((yg + sa.p) & 1u);  // parity of the target bit positions
+        for (uint32_t r = 0; r < R; ++r) {
+            Word *const qn = (y0 + r + 1 == rows) ? S + w : q + W;
+            const Word dn = *qn;
+            const Word lw = q[dl];
+            const Word rw = q[dr];
+            const Word nw = update_word<Word, INS>(a, sa, cur, up, dn, lw, rw, off, g, sa.acc != nullptr, cnt_up,
+                                                   cnt_anti);
+            *q = nw;
+            up = nw;
+            cur = dn;
+            q = qn;
+            g += groups_per_row;
+            off ^= 1u;
+        }
+        rb += a.stride_rb;
+        w += a.stride_w;
+        if (w >= W) {
+            w -= W;
+            ++rb;
+        }
+    }
 }
 
 }  // namespace

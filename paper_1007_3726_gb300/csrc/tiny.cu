@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
                 const uint32_t rw = lat[row + ((w + 1u) & (W - 1u))];
                 const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
                 const uint32_t nw =
-                    FIELD ? update_word_field(a, tab, A.k_up, A.k_dn, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca)
-                          : update_word<uint32_t, 0, NQ>(a, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca, sub * NQ);
+                    FIELD ? update_word_field(a, a, tab, A.k_up, A.k_dn, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca)
+                          : update_word<uint32_t, 0, NQ>(a, a, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca, sub * NQ);
                 if (NQ == 4)
                     lat[k] = nw;
                 else if (NQ == 2)
@@ -133,7 +133,11 @@ bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 
 LaunchConfig plain_launch(const LaunchConfig &c)
 {
-    if (c.proc_bits == 32 || c.proc_bits == 64) return c;
+    if (c.proc_bits == 32 || c.proc_bits == 64) {
+        LaunchConfig step = c;
+        step.persistent = 0;
+        return step;
+    }
     return LaunchConfig{32, 1, 0, 256, 2, 0};  // the step shape of small lattices
 }
 
