@@ -599,7 +599,11 @@ class Lattice:
         return ising_get_launch(self._h)
 
     def set_launch(self, **cfg):
+        """Replace the launch configuration; fields not given keep their current
+        values, except that naming proc_bits without persistent means persistent = 0."""
         full = dict(self.launch)
+        if "proc_bits" in cfg and "persistent" not in cfg:
+            full["persistent"] = 0
         full.update(cfg)
         ising_set_launch(self._h, full)
 

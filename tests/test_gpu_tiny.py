@@ -24,7 +24,7 @@ def P():
     return P
 
 
-TINY = {"proc_bits": 8, "regcap": 0, "insert": 0, "grid": 1}
+TINY = {"proc_bits": 8, "regcap": 0, "insert": 0, "grid": 1, "persistent": 0}
 
 
 @pytest.mark.parametrize("L", [64, 128, 256, 512, 1024])
