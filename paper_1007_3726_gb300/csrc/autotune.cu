@@ -43,8 +43,10 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
     }
     // untuned: the shapes the autotuner picked on GB300 at these sizes
     // (fields: proc_bits, regcap, insert, block, rows_per_item, grid)
-    if (L <= 128 && tiny_lattice_ok(L))  // one CTA, every sweep of a call in one launch
-        return L == 64 ? LaunchConfig{kTinyProcBits, 0, 0, 256, 2, 1} : LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 1};
+    // one CTA (L = 64) or a cluster of 8 CTAs (L = 128, 256): every sweep of a call in one launch
+    if (L == 64) return LaunchConfig{kTinyProcBits, 0, 0, 256, 2, 1};
+    if (L == 128) return LaunchConfig{kTinyProcBits, 0, 0, 128, 2, 8};
+    if (L == 256) return LaunchConfig{kTinyProcBits, 0, 0, 256, 1, 8};
     if (L < 4096) return LaunchConfig{32, 1, 0, 256, 2, 0};
     if (L < 16384) return LaunchConfig{64, 0, 0, 512, 4, 0};
     return LaunchConfig{64, 1, 0, 512, 8, 0};
@@ -60,11 +62,12 @@ std::vector<LaunchConfig> launch_candidates(uint64_t L, uint64_t rows)
 {
     std::vector<LaunchConfig> out;
     // the one-CTA kernel, for lattices one CTA holds
-    for (uint32_t blk : {128u, 256u, 512u})
-        for (uint32_t tpw : {1u, 2u, 4u}) {
-            LaunchConfig c{kTinyProcBits, 0, 0, blk, tpw, 1};
-            if (launch_config_valid(c, L, rows)) out.push_back(c);
-        }
+    for (uint32_t ctas : {1u, 2u, 4u, 8u})
+        for (uint32_t blk : {128u, 256u, 512u})
+            for (uint32_t tpw : {1u, 2u, 4u}) {
+                LaunchConfig c{kTinyProcBits, 0, 0, blk, tpw, ctas};
+                if (launch_config_valid(c, L, rows)) out.push_back(c);
+            }
     for (uint32_t pb : {32u, 64u})
         for (uint32_t rc : {0u, 1u, 2u})
             for (uint32_t ins : {0u, 1u, 2u})
@@ -202,10 +205,10 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
             ta.nrec = 0;
             ta.acc = h->d_acc;
             ta.nsweeps = 1;
-            e = launch_tiny(ta, c.block, c.rows_per_item, h->stream);
+            e = launch_tiny(ta, c.block, c.rows_per_item, c.grid, h->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
             ta.nsweeps = 8 * reps;
-            if (e == cudaSuccess) e = launch_tiny(ta, c.block, c.rows_per_item, h->stream);
+            if (e == cudaSuccess) e = launch_tiny(ta, c.block, c.rows_per_item, c.grid, h->stream);
             steps = 16 * reps;
         }
         for (uint32_t r = 0; r <= reps && e == cudaSuccess && c.proc_bits != kTinyProcBits && !c.persistent; ++r) {

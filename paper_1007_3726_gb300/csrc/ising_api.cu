@@ -421,7 +421,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
             ta.k_up = h->field.k_up;
             ta.k_dn = h->field.k_dn;
         }
-        CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->stream));
+        CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->launch.grid, h->stream));
         return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
     }
     if (h->launch.persistent && h->H == 0.0) {

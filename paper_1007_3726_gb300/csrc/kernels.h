@@ -62,7 +62,8 @@ cudaError_t launch_dependent(void (*kernel)(HalfSweepArgs), int grid, int block,
 // bit-identical results; they differ only in speed.  proc_bits == 8 selects the
 // one-CTA kernel of tiny.cu instead (whole lattice in shared memory, every
 // sweep of a call in one launch): block is its block size, rows_per_item the
-// threads that share one 32-bit word (1, 2 or 4), regcap = insert = 0, grid = 1.
+// threads that share one 32-bit word (1, 2 or 4), grid the CTAs (1, or a
+// cluster of 2, 4 or 8 that splits the rows), regcap = insert = 0.
 struct LaunchConfig {
     uint32_t proc_bits;      // 32 or 64: bits one thread updates per row; 8: one CTA
     uint32_t regcap;         // 0: compiler's choice, 1: <= 40 registers, 2: <= 32 registers
@@ -121,7 +122,9 @@ struct TinyRunArgs {
     uint32_t field_thr[16];
     uint32_t k_up, k_dn;
 };
-cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, cudaStream_t s);
+// ctas = 1: one CTA; 2, 4, 8: a cluster of CTAs, each with L / ctas rows.
+cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, uint32_t ctas,
+                        cudaStream_t s);
 // Resident blocks per SM of the configuration's kernel.
 int half_sweep_blocks_per_sm(const LaunchConfig &c);
 // Grid that makes every block resident (grid == 0 resolved).

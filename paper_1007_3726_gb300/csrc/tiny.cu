@@ -18,6 +18,8 @@
 #include "kernels.h"
 #include "sweep_device.cuh"
 
+#include <cooperative_groups.h>
+
 namespace ising {
 
 namespace {
@@ -120,6 +122,126 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
     for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = lat[i];
 }
 
+// The one-CTA kernel spread over a cluster of k = 2, 4 or 8 CTAs (distributed
+// shared memory): CTA c holds rows [c L/k, (c + 1) L/k) with one halo row above
+// and below.  At the start of each step it copies the halos from the
+// neighbouring CTAs' shared memory (their boundary rows as of the end of the
+// previous step; only the bits of the other parity are used, which nobody writes
+// during the step), and a cluster barrier ends the step.  A lattice too small to
+// fill one SM's issue slots gets k SMs.
+template <int NQ, bool FIELD>
+__global__ void __launch_bounds__(kTinyMaxThreads) k_tiny_cluster(const __grid_constant__ TinyRunArgs A)
+{
+    static_assert(!FIELD || NQ == 4, "the field update takes whole words");
+    constexpr uint32_t S = 4 / NQ;  // threads per word
+    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+    extern __shared__ uint32_t buf[];  // rows -1 .. rpc of this CTA, W words each
+    __shared__ unsigned int cnt[2];
+    __shared__ uint32_t tab[16];
+    if (FIELD && threadIdx.x < 16) tab[threadIdx.x] = A.field_thr[threadIdx.x];
+    const uint32_t L = (uint32_t)A.L;
+    const uint32_t W = L >> 5;  // words per row, a power of two
+    const uint32_t lgW = 31 - __clz(W);
+    const uint32_t k = cluster.num_blocks(), c = cluster.block_rank();
+    const uint32_t rpc = L / k;  // rows of this CTA
+    const uint32_t row0 = c * rpc;
+    const uint32_t nwords = rpc * W;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    const uint64_t groups_per_row = L >> 3;
+    uint32_t *const own = buf + W;
+
+    const uint32_t *src = static_cast<const uint32_t *>(A.spins) + (uint64_t)row0 * W;
+    for (uint32_t i = tid; i < nwords; i += nthr) own[i] = src[i];
+    if (tid < 2) cnt[tid] = 0u;
+    // the neighbouring CTAs' buffers (their own rows start one row in)
+    const uint32_t *const prev = cluster.map_shared_rank(buf, (c + k - 1) % k);
+    const uint32_t *const next = cluster.map_shared_rank(buf, (c + 1) % k);
+    cluster.sync();
+
+    HalfSweepArgs a;
+    a.key = A.key;
+    a.thr4 = A.thr4;
+    a.thr8 = A.thr8;
+    a.zero = 0u;
+    uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;  // t % record_every
+    uint32_t slot = 0;
+    for (uint32_t i = 0; i < A.nsweeps; ++i) {
+        const uint32_t t = A.t0 + i;
+        const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
+        const bool last = i + 1 == A.nsweeps;
+        const uint64_t pb = (uint64_t)t * kPhiloxMulB;
+        a.r1x0 = (uint32_t)(pb >> 32) ^ A.key.k0[0];
+        a.r2x0k = (uint32_t)pb ^ A.key.k0[1];
+        const uint64_t pa = (uint64_t)a.r1x0 * kPhiloxMulA;
+        a.r2x2k = (uint32_t)(pa >> 32) ^ A.key.k1[1];
+        a.r2x3 = (uint32_t)pa;
+#pragma unroll 1
+        for (uint32_t p = 0; p < 2; ++p) {
+            a.r1x2k = (A.c3base | p) ^ A.key.k1[0];
+            const bool count = p == 1u && (rec || last);
+            // halos: the previous CTA's last row above, the next CTA's first row below
+            for (uint32_t j = tid; j < 2 * W; j += nthr) {
+                if (j < W)
+                    buf[j] = prev[W + (rpc - 1) * W + j];
+                else
+                    buf[(rpc + 1) * W + (j - W)] = next[W + (j - W)];
+            }
+            __syncthreads();
+            unsigned int cu = 0, ca = 0;
+            for (uint32_t it = tid; it < nwords * S; it += nthr) {
+                const uint32_t kw = it / S, sub = it % S;  // S is a power of two
+                const uint32_t ly = kw >> lgW, w = kw & (W - 1u);
+                uint32_t *const row = own + ly * W;  // rows ly - 1 and ly + 1 are in buf as well
+                const uint32_t cur = row[w];
+                const uint32_t up = row[w - W];
+                const uint32_t dn = row[w + W];
+                const uint32_t lw = row[(w - 1u) & (W - 1u)];
+                const uint32_t rw = row[(w + 1u) & (W - 1u)];
+                const uint32_t y = row0 + ly;
+                const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
+                const uint32_t nw =
+                    FIELD ? update_word_field(a, a, tab, A.k_up, A.k_dn, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca)
+                          : update_word<uint32_t, 0, NQ>(a, a, cur, up, dn, lw, rw, (y + p) & 1u, g, count, cu, ca, sub * NQ);
+                if (NQ == 4)
+                    row[w] = nw;
+                else if (NQ == 2)
+                    reinterpret_cast<uint16_t *>(row + w)[sub] = (uint16_t)(nw >> (16 * sub));
+                else
+                    reinterpret_cast<uint8_t *>(row + w)[sub] = (uint8_t)(nw >> (8 * sub));
+            }
+            if (count) {
+                cu = __reduce_add_sync(0xFFFFFFFFu, cu);
+                ca = __reduce_add_sync(0xFFFFFFFFu, ca);
+                if ((tid & 31u) == 0) {
+                    atomicAdd(&cnt[0], cu);
+                    atomicAdd(&cnt[1], ca);
+                }
+            }
+            cluster.sync();  // the step is complete in every CTA
+            if (count && tid == 0) {
+                // the CTAs' counts add up in the sample slots; the next counted step
+                // is two steps and two barriers away
+                const unsigned long long c0 = cnt[0], c1 = cnt[1];
+                if (rec) {
+                    atomicAdd(A.acc + 2 * slot, c0);
+                    atomicAdd(A.acc + 2 * slot + 1, c1);
+                }
+                if (last) {
+                    atomicAdd(A.acc + 2 * A.nrec, c0);
+                    atomicAdd(A.acc + 2 * A.nrec + 1, c1);
+                }
+                cnt[0] = 0u;
+                cnt[1] = 0u;
+            }
+        }
+        if (rec) ++slot;
+        if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
+    }
+    uint32_t *dst = static_cast<uint32_t *>(A.spins) + (uint64_t)row0 * W;
+    for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = own[i];
+    cluster.sync();  // no CTA leaves while another may still read its buffer
+}
+
 }  // namespace
 
 bool tiny_lattice_ok(uint64_t L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
@@ -128,7 +250,8 @@ bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
     return c.proc_bits == kTinyProcBits && tiny_lattice_ok(L) && rows == L && c.regcap == 0 && c.insert == 0 &&
            (c.block == 128 || c.block == 256 || c.block == 512) &&
-           (c.rows_per_item == 1 || c.rows_per_item == 2 || c.rows_per_item == 4) && c.grid == 1;
+           (c.rows_per_item == 1 || c.rows_per_item == 2 || c.rows_per_item == 4) &&
+           (c.grid == 1 || c.grid == 2 || c.grid == 4 || c.grid == 8) && c.persistent == 0;
 }
 
 LaunchConfig plain_launch(const LaunchConfig &c)
@@ -141,22 +264,49 @@ LaunchConfig plain_launch(const LaunchConfig &c)
     return LaunchConfig{32, 1, 0, 256, 2, 0};  // the step shape of small lattices
 }
 
-cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, cudaStream_t s)
+cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, uint32_t ctas,
+                        cudaStream_t s)
 {
     if (!tiny_lattice_ok(a.L) || a.nsweeps == 0 || block == 0 || block > kTinyMaxThreads || block % 32 != 0)
         return cudaErrorInvalidValue;
-    void (*kern)(TinyRunArgs) = a.use_field                ? k_tiny<4, true>
-                                : threads_per_word == 1 ? k_tiny<4, false>
-                                : threads_per_word == 2 ? k_tiny<2, false>
-                                : threads_per_word == 4 ? k_tiny<1, false> : nullptr;
+    if (ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8) return cudaErrorInvalidValue;
+    using TinyKernel = void (*)(TinyRunArgs);
+    TinyKernel kern;
+    if (ctas == 1)
+        kern = a.use_field ? k_tiny<4, true>
+               : threads_per_word == 1 ? k_tiny<4, false>
+               : threads_per_word == 2 ? k_tiny<2, false>
+               : threads_per_word == 4 ? k_tiny<1, false> : nullptr;
+    else
+        kern = a.use_field ? k_tiny_cluster<4, true>
+               : threads_per_word == 1 ? k_tiny_cluster<4, false>
+               : threads_per_word == 2 ? k_tiny_cluster<2, false>
+               : threads_per_word == 4 ? k_tiny_cluster<1, false> : nullptr;
     if (!kern) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(a.L * a.L / 8);
+    // the whole lattice, or a CTA's rows and its two halo rows
+    const size_t W = a.L / 32;
+    const size_t smem = ctas == 1 ? (size_t)(a.L * W * 4) : (size_t)((a.L / ctas + 2) * W * 4);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<1, block, smem, s>>>(a);
-    return cudaGetLastError();
+    if (ctas == 1) {
+        kern<<<1, block, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = ctas;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 }  // namespace ising

@@ -132,7 +132,7 @@ def test_launch_candidates_are_listed_without_a_gpu(ising):
     assert all(32768 % x["rows_per_item"] == 0 for x in c)
     assert len(ising.ising_launch_candidates(192)) >= 162
     # the one-CTA kernel is a candidate exactly for power-of-two L <= 1024
-    for L, k in ((64, 9), (256, 9), (1024, 9), (192, 0), (2048, 0), (32768, 0)):
+    for L, k in ((64, 36), (256, 36), (1024, 36), (192, 0), (2048, 0), (32768, 0)):
         assert sum(x["proc_bits"] == 8 for x in ising.ising_launch_candidates(L)) == k, L
     # L = 2^20: configurations whose item count does not fit 32 bits are left out
     big = ising.ising_launch_candidates(2 ** 20)

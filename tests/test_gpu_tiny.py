@@ -2,7 +2,7 @@
 sweep of a call in one launch; launch configurations with proc_bits == 8),
 against the oracle, bit for bit.
 
-It is the default for L <= 128, so the other parity tests at those sizes run
+It is the default for L <= 256, so the other parity tests at those sizes run
 through it too; here every block size and every size it takes (64 .. 1024, up
 to 128 KiB of shared memory and 256 bytes per thread) is checked, with samples
 recorded every sweep, every third sweep across split calls, and not at all.
@@ -91,7 +91,8 @@ def test_tiny_is_rejected_where_it_does_not_apply(P):
             lat.set_launch(**TINY, block=256, rows_per_item=1)
         lat.close()
     lat = P.Lattice(64, 2.0, seed=1)
-    for bad in ({"block": 1024}, {"grid": 2}, {"rows_per_item": 3}, {"rows_per_item": 8}, {"regcap": 1}):
+    for bad in ({"block": 1024}, {"grid": 3}, {"grid": 16}, {"rows_per_item": 3}, {"rows_per_item": 8},
+                {"regcap": 1}):
         cfg = dict(TINY, block=256, rows_per_item=1)
         cfg.update(bad)
         with pytest.raises(P.IsingError):
@@ -134,3 +135,31 @@ def test_tiny_in_a_field_bit_exact(P, orc, L, H):
     recorded = [i for i in range(4) if (n + i + 1) % 2 == 0]  # sweep t is recorded when (t + 1) % 2 == 0
     assert np.array_equal(M2, Mo2[recorded])
     assert np.array_equal(lat.spins(), s)
+
+
+@pytest.mark.parametrize("L", [64, 128, 256, 1024])
+@pytest.mark.parametrize("ctas", [2, 4, 8])
+@pytest.mark.parametrize("tpw", [1, 4])
+def test_tiny_cluster_bit_exact(P, orc, L, ctas, tpw):
+    """A thread-block cluster of 2, 4 or 8 CTAs sharing one lattice (each holds
+    L / ctas rows and reads its halo rows from its neighbours' shared memory)."""
+    n = 10 if L <= 256 else 3
+    T, seed, sid = 2.2, L + ctas + tpw, 3
+    lat = P.Lattice(L, T, seed=seed, stream_id=sid, init="hot")
+    lat.set_launch(**dict(TINY, grid=ctas), block=256, rows_per_item=tpw)
+    M, E = lat.sweep(n, 1, collect=True)
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_hot(L, seed, sid)
+    Mo, Eo = orc.run(s, n, seed, sid, thr4, thr8)
+    assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
+    assert np.array_equal(lat.spins(), s)
+    # sparse records over split calls, then a field
+    M2, _ = lat.sweep(7, 3, collect=True)
+    Mo2, _ = orc.run(s, 7, seed, sid, thr4, thr8, t0=n)
+    assert np.array_equal(M2, Mo2[[i for i in range(7) if (n + i + 1) % 3 == 0]])
+    lat.set_field(0.7)
+    M3, E3 = lat.sweep(4, 1, collect=True)
+    Mo3, Eo3 = orc.run_field(s, 4, seed, sid, T, 0.7, t0=n + 7)
+    assert np.array_equal(M3, Mo3) and np.array_equal(E3, Eo3)
+    assert np.array_equal(lat.spins(), s)
+    lat.close()
