@@ -227,7 +227,7 @@ ISING_API const char *ising_last_error(void);
  * grid the CTAs: 1, or a thread-block cluster of 2, 4 or 8 CTAs that split
  * the rows and read their neighbours' boundary rows from distributed shared
  * memory, with a cluster barrier between the steps; regcap = insert = 0.  It is
- * the default for L <= 256 (one CTA at L = 64, a cluster of 8 above).  In a
+ * the default for L <= 512 (one CTA at L = 64, a cluster of 8 above).  In a
  * field (H != 0) it uses one thread per word whatever rows_per_item says; the
  * step kernels are then replaced by the field step kernel.
  * persistent = 1 (with proc_bits 32 or 64, insert 0, grid 0; regcap 0, 1 or

@@ -43,10 +43,11 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
     }
     // untuned: the shapes the autotuner picked on GB300 at these sizes
     // (fields: proc_bits, regcap, insert, block, rows_per_item, grid)
-    // one CTA (L = 64) or a cluster of 8 CTAs (L = 128, 256): every sweep of a call in one launch
+    // one CTA (L = 64) or a cluster of 8 CTAs (L = 128 .. 512): every sweep of a call in one launch
     if (L == 64) return LaunchConfig{kTinyProcBits, 0, 0, 256, 2, 1};
     if (L == 128) return LaunchConfig{kTinyProcBits, 0, 0, 128, 2, 8};
     if (L == 256) return LaunchConfig{kTinyProcBits, 0, 0, 256, 1, 8};
+    if (L == 512) return LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 8};
     if (L < 4096) return LaunchConfig{32, 1, 0, 256, 2, 0};
     if (L < 16384) return LaunchConfig{64, 0, 0, 512, 4, 0};
     return LaunchConfig{64, 1, 0, 512, 8, 0};

@@ -2,7 +2,7 @@
 sweep of a call in one launch; launch configurations with proc_bits == 8),
 against the oracle, bit for bit.
 
-It is the default for L <= 256, so the other parity tests at those sizes run
+It is the default for L <= 512, so the other parity tests at those sizes run
 through it too; here every block size and every size it takes (64 .. 1024, up
 to 128 KiB of shared memory and 256 bytes per thread) is checked, with samples
 recorded every sweep, every third sweep across split calls, and not at all.
