@@ -216,9 +216,12 @@ ISING_API const char *ising_last_error(void);
  *   block          threads per block: 128, 256 or 512
  *   rows_per_item  rows one thread walks down per work item (divides L, <= 64)
  *   grid           blocks, 0 = as many as can be resident at once
- *   insert         0, 1 or 2: how many of the two acceptance masks (u < thr4,
- *                  u < thr8) are built with logic operations rather than
- *                  additions (a balance between two integer pipelines)
+ *   insert         0, 1 or 2: how a compare's result (u < thr4, u < thr8)
+ *                  becomes a mask bit: 0 a predicated OR on the integer
+ *                  pipes; 1 a predicated FP32 add of 4^k into one exact
+ *                  per-8-site counter of both compares; 2 the same into
+ *                  separate P4 and P8 counters (FP32 adds issue on the FMA
+ *                  pipe that the Philox multiplies leave idle)
  * proc_bits = 8 selects instead the one-CTA form for lattices one thread block
  * holds (L a power of two, 64 <= L <= 1024): the whole lattice stays in shared
  * memory and every sweep of an ising_sweep call runs in one launch, with a
@@ -260,6 +263,25 @@ ISING_API uint32_t ising_launch_candidates(uint64_t L, ising_launch *out, uint32
  */
 ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_launch *best,
                                       double *best_us_per_step);
+
+/*
+ * ising_bench_mix - the integer-mix microbenchmark: how fast this GPU generates
+ * the sweep's Philox4x32-10 draws alone (the random numbers of Sec. 5.3's role,
+ * in the counter-based form of this library), timed with CUDA events on
+ * cuda_stream over one launch of one full wave of resident 512-thread blocks,
+ * after one untimed warm-up launch.  Each thread makes the eight calls (32
+ * draws) of a 64-bit word, words_per_thread times (1 .. 2^20), in form
+ *   0  ten full Philox rounds per call (2 widening multiplies and 2
+ *      three-input XORs per round);
+ *   1  the half-sweep's own form of the calls (rounds 1-2 partly hoisted);
+ *   2  form 1 plus the acceptance masks (two compares and bit insertions per
+ *      draw), i.e. the word update without its lattice logic and memory.
+ * Outputs: *ms the launch's time, *draws_per_ns the draws per nanosecond.
+ * Allocates (and frees) one word per thread of device memory; waits for the
+ * GPU.  Errors: ISING_ERR_INVALID for a bad form or size, ISING_ERR_CUDA.
+ */
+ISING_API ising_status ising_bench_mix(uint32_t form, uint32_t words_per_thread, double *ms,
+                                       double *draws_per_ns, void *cuda_stream);
 
 /* ---- many lattices in one persistent launch ----------------------------- */
 
@@ -417,14 +439,20 @@ ISING_API ising_status ising_strip_step(void *d_rows, uint64_t L, uint32_t word_
  * It runs nsweeps sweeps t0 .. t0 + nsweeps - 1 (the same arithmetic and the
  * same results as ising_sweep on a handle whose sweeps_done is t0) on a lattice
  * the caller owns: d_spins is the caller's device array of L * L / 8 bytes in
- * the storage layout above with word_bits-bit words, updated in place.  The
+ * the storage layout above with word_bits-bit words, updated in place.  It
+ * must be memory of the current device (cudaMalloc'd or managed) and 16-byte
+ * aligned, since the kernels read it in units of up to 128 bits whatever the
+ * storage width; anything else fails with ISING_ERR_INVALID before any work.
+ * Lattices that ising_sweep runs in one launch (one CTA or one cluster,
+ * L <= 512 by default) run the same way here; larger ones take two step
+ * launches per sweep.  The
  * samples (M, E) of the sweeps whose count t + 1 is a multiple of
  * record_every (0 = none) go to the caller's host arrays M_out / E_out (cap
  * entries each) and the call then waits for cuda_stream; with no sample the
  * call returns once the work is queued.
  *
  * Scratch: the per-sweep counters live in a fixed device array compiled into
- * the library, ISING_NOALLOC_MAX_RECORDS samples (1 MiB) that every GPU which
+ * the library, ISING_NOALLOC_MAX_RECORDS samples plus one slot (1 MiB) that every GPU which
  * loads the library holds until the process exits.  A call that would record
  * more samples fails with ISING_ERR_INVALID before any work; split it.  All
  * calls share that array and it keeps the previous call's contents (the call

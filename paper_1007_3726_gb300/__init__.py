@@ -22,7 +22,7 @@ __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
     "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount", "ising_get_samples",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
-    "ising_device_spins", "ising_sweep_noalloc", "ising_strip_init", "ising_strip_step", "ising_get_launch", "ising_set_launch",
+    "ising_device_spins", "ising_sweep_noalloc", "ising_bench_mix", "ising_strip_init", "ising_strip_step", "ising_get_launch", "ising_set_launch",
     "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "Server", "IsingBatchOpts",
     "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
@@ -178,6 +178,8 @@ def load(path: str | None = None):
         "ising_set_field": ([H, ctypes.c_double], ctypes.c_int),
         "ising_get_params": ([H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                              ctypes.c_int),
+        "ising_bench_mix": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.c_uint32, _i64p, _i64p, ctypes.c_uint64, ctypes.c_void_p],
@@ -313,11 +315,28 @@ def ising_sweep_noalloc(d_spins: int, L: int, word_bits: int, T: float, seed: in
                         t0: int, nsweeps: int, record_every: int = 0, M_out=None, E_out=None,
                         cap: int = 0, stream=None):
     """Sweeps on a caller-owned device lattice without any allocation by the
-    library (see include/ising.h); M_out / E_out are host int64 arrays."""
+    library (see include/ising.h); M_out / E_out are host int64 arrays of at
+    least cap entries (C-contiguous), or both None."""
+    for name, arr in (("M_out", M_out), ("E_out", E_out)):
+        if arr is None:
+            continue
+        if not (isinstance(arr, np.ndarray) and arr.dtype == np.int64 and arr.flags.c_contiguous
+                and arr.flags.writeable and arr.size >= cap):
+            raise ValueError("%s must be a writeable C-contiguous int64 array of at least cap = %d "
+                             "entries" % (name, cap))
     mp = M_out.ctypes.data_as(_i64p) if M_out is not None else None
     ep = E_out.ctypes.data_as(_i64p) if E_out is not None else None
     _check(load().ising_sweep_noalloc(d_spins, L, word_bits, float(T), seed, stream_id, t0, nsweeps,
                                       record_every, mp, ep, cap, _stream_ptr(stream)))
+
+
+def ising_bench_mix(form: int, words_per_thread: int, stream=None) -> tuple[float, float]:
+    """The integer-mix microbenchmark (see include/ising.h): (ms, draws per ns)."""
+    ms = ctypes.c_double()
+    rate = ctypes.c_double()
+    _check(load().ising_bench_mix(form, words_per_thread, ctypes.byref(ms), ctypes.byref(rate),
+                                  _stream_ptr(stream)))
+    return ms.value, rate.value
 
 
 def ising_get_launch(h) -> dict:

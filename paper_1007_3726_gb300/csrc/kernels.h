@@ -67,7 +67,7 @@ cudaError_t launch_dependent(void (*kernel)(HalfSweepArgs), int grid, int block,
 struct LaunchConfig {
     uint32_t proc_bits;      // 32 or 64: bits one thread updates per row; 8: one CTA
     uint32_t regcap;         // 0: compiler's choice, 1: <= 40 registers, 2: <= 32 registers
-    uint32_t insert;         // acceptance-bit insertion kept on the ALU pipe: 0 none, 1 P4, 2 P4+P8
+    uint32_t insert;         // acceptance-bit insertion: 0 predicated OR, 1 FP32 counts, 2 FP32 masks
     uint32_t block;          // 128, 256 or 512 threads
     uint32_t rows_per_item;  // 2 .. 64, divides L
     uint32_t grid;           // blocks (0 = all resident blocks of the device)

@@ -5,8 +5,9 @@
 // HBM budget up front in its own pool, a host application that lends device
 // buffers to plug-ins and forbids them the CUDA allocator, or a loop that
 // cannot afford the device-wide synchronisation a cudaMalloc / cudaFree may
-// bring.  For them this entry point runs the same half-sweep kernel as
-// ising_sweep on a lattice the caller owns, and keeps the kernel's scratch
+// bring.  For them this entry point runs ising_sweep's kernels on a lattice the
+// caller owns (the one-CTA or cluster kernel where ising_sweep's default takes
+// it, the half-sweep step kernels otherwise), and keeps the kernels' scratch
 // (the per-sweep M/E counters) in a fixed array compiled into the library
 // instead of allocating it.
 #include "ising.h"
@@ -14,6 +15,7 @@
 #include "kernels.h"
 #include "runtime.h"
 
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -22,10 +24,11 @@ using namespace ising;
 namespace {
 
 // Two 64-bit counters per recorded sweep (number of +1 spins, number of
-// anti-aligned bonds).  Every GPU that loads the library holds this 1 MiB
-// until the process exits.
+// anti-aligned bonds), plus one slot for the state after the call's last sweep
+// that the one-CTA and cluster kernels always write.  Every GPU that loads the
+// library holds this 1 MiB (and 16 bytes) until the process exits.
 constexpr uint64_t kMaxRecords = ISING_NOALLOC_MAX_RECORDS;
-static __device__ __align__(256) unsigned long long g_noalloc_counters[2 * kMaxRecords];
+static __device__ __align__(256) unsigned long long g_noalloc_counters[2 * (kMaxRecords + 1)];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -63,13 +66,32 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
 {
     clear_error();
     if (!d_spins) return fail(ISING_ERR_INVALID, "d_spins is NULL");
+    // the kernels read the lattice in 32- to 128-bit units whatever word_bits it
+    // was stored with
+    if (reinterpret_cast<uintptr_t>(d_spins) % 16 != 0)
+        return fail(ISING_ERR_INVALID, "d_spins must be 16-byte aligned");
     if (L < 64 || L % 64 != 0 || L > (1ull << 20))
         return fail(ISING_ERR_INVALID, "L must be a multiple of 64 in [64, 2^20]");
     if (word_bits != 32 && word_bits != 64) return fail(ISING_ERR_INVALID, "word_bits must be 32 or 64");
     if (!valid_temperature(T)) return fail(ISING_ERR_INVALID, "T must be finite and > 0");
     if (stream_id >= (1u << 31)) return fail(ISING_ERR_INVALID, "stream_id must be < 2^31");
-    if (t0 + nsweeps >= 0xFFFFFFFFull)
+    if (t0 >= 0xFFFFFFFFull || nsweeps >= 0xFFFFFFFFull - t0)
         return fail(ISING_ERR_INVALID, "sweep counter would reach 2^32 - 1");
+    {
+        // device (or managed) memory of the current device only: a host pointer
+        // or another GPU's memory is refused before any work
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return fail(ISING_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+        cudaPointerAttributes pa{};
+        e = cudaPointerGetAttributes(&pa, d_spins);
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // not sticky: clear it
+            return fail(ISING_ERR_INVALID, "d_spins is not device memory (%s)", cudaGetErrorString(e));
+        }
+        if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+            return fail(ISING_ERR_INVALID, "d_spins must be device memory of the current device %d", dev);
+    }
     if ((M_out == nullptr) != (E_out == nullptr))
         return fail(ISING_ERR_INVALID, "M_out and E_out must both be set or both be NULL");
     const uint64_t nrec = record_every ? (t0 + nsweeps) / record_every - t0 / record_every : 0;
@@ -99,9 +121,29 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
     a.thr8 = threshold_for(8.0, T);
     int dev = 0;
     cudaGetDevice(&dev);
-    const LaunchConfig cfg = plain_launch(default_launch(dev, L, word_bits));
+    const LaunchConfig dflt = default_launch(dev, L, word_bits);
+    if (dflt.proc_bits == kTinyProcBits) {
+        // a lattice that one CTA or one cluster holds: every sweep in one launch,
+        // as ising_sweep runs it; its last slot (after the final sweep) is unused here
+        TinyRunArgs ta{};
+        ta.spins = d_spins;
+        ta.L = L;
+        ta.key = a.key;
+        ta.thr4 = a.thr4;
+        ta.thr8 = a.thr8;
+        ta.c3base = stream_id << 1;
+        ta.t0 = (uint32_t)t0;
+        ta.nsweeps = (uint32_t)nsweeps;
+        ta.record_every = record_every;
+        ta.nrec = (uint32_t)nrec;
+        ta.acc = acc;
+        // the cluster kernel adds into every slot it writes, the last one included
+        e = cudaMemsetAsync(acc, 0, (nrec + 1) * 2 * sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = launch_tiny(ta, dflt.block, dflt.rows_per_item, dflt.grid, s);
+    }
+    const LaunchConfig cfg = plain_launch(dflt);
     uint64_t slot = 0;
-    for (uint64_t i = 0; i < nsweeps && e == cudaSuccess; ++i) {
+    for (uint64_t i = 0; dflt.proc_bits != kTinyProcBits && i < nsweeps && e == cudaSuccess; ++i) {
         const uint64_t t = t0 + i;
         a.t = (uint32_t)t;
         for (uint32_t p = 0; p < 2 && e == cudaSuccess; ++p) {

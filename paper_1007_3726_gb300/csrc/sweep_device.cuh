@@ -161,42 +161,146 @@ __device__ __forceinline__ void word_draw_call(const K &k, const S &s, const Wor
     u[3] = y3;
 }
 
+// Bit insertion of one compare, u < thr, for the FP32 forms of
+// word_draw_masks: the predicated add of 4^M to an FP32 accumulator.  The
+// accumulator starts at 2^23 and only ever holds integers below 2^24, so
+// every add is exact; its low 16 bits are then the sum of the weights added.
+// The weights are immediates (4^M as a PTX hex float) so that no register
+// holds them.
+template <int M>
+__device__ __forceinline__ void fadd_if_below(float &acc, uint32_t u, uint32_t thr)
+{
+#define ISING_FADD_IF_BELOW(HEX)                                                              \
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p add.f32 %0, %0, 0f" HEX ";\n\t}" \
+        : "+f"(acc)                                                                           \
+        : "r"(u), "r"(thr))
+    static_assert(M >= 0 && M < 8, "weights 4^0 .. 4^7");
+    if constexpr (M == 0) ISING_FADD_IF_BELOW("3F800000");
+    if constexpr (M == 1) ISING_FADD_IF_BELOW("40800000");
+    if constexpr (M == 2) ISING_FADD_IF_BELOW("41800000");
+    if constexpr (M == 3) ISING_FADD_IF_BELOW("42800000");
+    if constexpr (M == 4) ISING_FADD_IF_BELOW("43800000");
+    if constexpr (M == 5) ISING_FADD_IF_BELOW("44800000");
+    if constexpr (M == 6) ISING_FADD_IF_BELOW("45800000");
+    if constexpr (M == 7) ISING_FADD_IF_BELOW("46800000");
+#undef ISING_FADD_IF_BELOW
+}
+
+constexpr float kTwoTo23 = 8388608.0f;
+
+// Bytes 0-1 of lo and bytes 0-1 of hi as one word (the low 16 bits of two
+// accumulators started at 2^23).
+__device__ __forceinline__ uint32_t low_halves(float lo, float hi)
+{
+    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x5410);
+}
+
+// The draws of call qq (at local position qq of the calls this thread draws)
+// added into the FP32 accumulators: site k = 4 (qq & 3) + l of a 32-bit half
+// gets weight 4^(k mod 8) in accumulator (qq >> 1) & 1 of that half.  With
+// SEP the P4 and P8 compares go to separate accumulators (f4, f8), else both
+// into f4, which then holds the per-site count [u < thr4] + [u < thr8] in 0..2.
+template <int QQ, int L, bool SEP>
+__device__ __forceinline__ void fadd_site(float &f4, float &f8, uint32_t u, uint32_t thr4, uint32_t thr8)
+{
+    constexpr int M = 4 * (QQ & 1) + L;
+    fadd_if_below<M>(f4, u, thr4);
+    fadd_if_below<M>(SEP ? f8 : f4, u, thr8);
+}
+
+template <int QQ, bool SEP, int NH>
+__device__ __forceinline__ void fadd_call(float (&f4)[NH][2], float (&f8)[NH][2], const uint32_t (&u)[4], int h,
+                                          uint32_t thr4, uint32_t thr8)
+{
+    constexpr int j = (QQ >> 1) & 1;
+    fadd_site<QQ, 0, SEP>(f4[h][j], f8[h][j], u[0], thr4, thr8);
+    fadd_site<QQ, 1, SEP>(f4[h][j], f8[h][j], u[1], thr4, thr8);
+    fadd_site<QQ, 2, SEP>(f4[h][j], f8[h][j], u[2], thr4, thr8);
+    fadd_site<QQ, 3, SEP>(f4[h][j], f8[h][j], u[3], thr4, thr8);
+}
+
+template <int QQ, int NQ, int NB, bool SEP, int NH, typename K, typename S>
+__device__ __forceinline__ void fadd_calls(const K &a, const S &s, const WordDraws &d, uint32_t q0,
+                                           float (&f4)[NH][2], float (&f8)[NH][2])
+{
+    if constexpr (QQ < NQ) {
+        const uint32_t q = (NQ == NB) ? (uint32_t)QQ : q0 + (uint32_t)QQ;
+        uint32_t u[4];
+        word_draw_call(a, s, d, q, u);
+        fadd_call<QQ, SEP>(f4, f8, u, (NQ == NB) ? (QQ >> 2) : 0, a.thr4, a.thr8);
+        fadd_calls<QQ + 1, NQ, NB, SEP>(a, s, d, q0, f4, f8);
+    }
+}
+
 // The acceptance masks of one word whose first Philox group is g0: bit
 // 8q + 2l of half (q / 4) is set when draw l of the word's call q is below the
-// threshold.
+// threshold.  INS selects how a compare's result becomes a bit:
+//   0  a predicated OR into an integer mask;
+//   1  a predicated FP32 add into one accumulator per 8 sites that counts
+//      [u < thr4] + [u < thr8] (two bits per site, decoded into both masks);
+//   2  predicated FP32 adds into separate P4 and P8 accumulators.
+// The integer OR (or the addition the compiler makes of it) issues on the pipe
+// that carries the Philox multiplies; the FP32 adds issue on the other FMA
+// pipe, which the rest of the update leaves idle.  Forms 1 and 2 relieve the
+// multiply pipe (its busy share falls from 81 % to 66 %) but measured 4 %
+// slower on GB300: the autotuner keeps them as candidates.
 template <int NB, int INS, int NQ = NB, typename K, typename S>
 __device__ __forceinline__ void word_draw_masks(const K &a, const S &s, uint64_t g0,
                                                 uint32_t (&p4)[(NB + 3) / 4],
                                                 uint32_t (&p8)[(NB + 3) / 4], uint32_t q0 = 0)
 {
+    static_assert(INS >= 0 && INS <= 2, "insertion forms 0, 1, 2");
     const WordDraws d = word_draws_begin(a, s, g0);
-    // INS >= 1 (>= 2) starts the P4 (P8) mask from a zero the compiler cannot
-    // see, so that its bit insertions stay ORs on the ALU pipe instead of
-    // becoming additions on the pipe that also carries the Philox multiplies.
     // With NQ < NB the calls q0 .. q0 + NQ - 1 (within one 32-bit half, since q0
     // is a multiple of NQ <= 4) are accumulated at their offsets from q0.
     constexpr int NH = (NQ == NB) ? (NB + 3) / 4 : 1;
     uint32_t m4[NH], m8[NH];
+    if constexpr (INS == 0) {
 #pragma unroll
-    for (int h = 0; h < NH; ++h) {
-        m4[h] = INS >= 1 ? a.zero : 0u;
-        m8[h] = INS >= 2 ? a.zero : 0u;
-    }
+        for (int h = 0; h < NH; ++h) {
+            m4[h] = 0u;
+            m8[h] = 0u;
+        }
 #pragma unroll
-    for (int qq = 0; qq < NQ; ++qq) {
-        const uint32_t q = (NQ == NB) ? (uint32_t)qq : q0 + (uint32_t)qq;
-        uint32_t u[4];
-        word_draw_call(a, s, d, q, u);
-        const int h = (NQ == NB) ? (qq >> 2) : 0;
+        for (int qq = 0; qq < NQ; ++qq) {
+            const uint32_t q = (NQ == NB) ? (uint32_t)qq : q0 + (uint32_t)qq;
+            uint32_t u[4];
+            word_draw_call(a, s, d, q, u);
+            const int h = (NQ == NB) ? (qq >> 2) : 0;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const uint32_t bit = 1u << (8 * (qq & 3) + 2 * l);
-            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
-                : "+r"(m4[h])
-                : "r"(u[l]), "r"(a.thr4), "r"(bit));
-            asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
-                : "+r"(m8[h])
-                : "r"(u[l]), "r"(a.thr8), "r"(bit));
+            for (int l = 0; l < 4; ++l) {
+                const uint32_t bit = 1u << (8 * (qq & 3) + 2 * l);
+                asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+                    : "+r"(m4[h])
+                    : "r"(u[l]), "r"(a.thr4), "r"(bit));
+                asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+                    : "+r"(m8[h])
+                    : "r"(u[l]), "r"(a.thr8), "r"(bit));
+            }
+        }
+    } else {
+        constexpr bool SEP = INS == 2;
+        float f4[NH][2], f8[NH][2];
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                f4[h][j] = kTwoTo23;
+                f8[h][j] = kTwoTo23;
+            }
+        fadd_calls<0, NQ, NB, SEP>(a, s, d, q0, f4, f8);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const uint32_t v = low_halves(f4[h][0], f4[h][1]);
+            if constexpr (SEP) {
+                m4[h] = v;
+                m8[h] = low_halves(f8[h][0], f8[h][1]);
+            } else {
+                // per site two bits: 1 = P4 only, 2 = P4 and P8 (thr8 < thr4)
+                const uint32_t hi = v >> 1;
+                m8[h] = hi & 0x55555555u;
+                m4[h] = (v | hi) & 0x55555555u;
+            }
         }
     }
     if (NQ == NB) {
