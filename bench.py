@@ -1,25 +1,36 @@
 #!/usr/bin/env python3
 """Benchmark of the multi-spin-coded checkerboard Metropolis sweep on GB300.
 
-Workload (one step): 1000 sweeps of the L = 32768 lattice (2^30 spins, 32 spins
-per 32-bit word, 128 MiB), hot start from seed 7, T = 2.269185, M and E
-recorded after every sweep, then the FP64 moments.  Metric: spin-flip
+Workload: the largest single-GPU lattice, L = 524288 (2^38 spins, 64 spins per
+64-bit word, 32 GiB), cold start, T = 2.0, seed 5, M and E recorded after every
+sweep.  A step is 10 sweeps (the 200-sweep run is 20 steps).  Metric: spin-flip
 attempts per ns (N = L^2 attempts per sweep).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--parallelism replicas|strips]
 
-Under torchrun (N > 1) every rank runs its own replica lattice (stream_id =
-rank); the units of all ranks are summed over the slowest rank's time.
+--gpus N with N > 1 starts N ranks itself (torch.distributed.run on this node)
+unless it already runs under a launcher that set WORLD_SIZE, which must then
+equal N.  Ranks:
+  replicas  every rank sweeps its own L = 524288 lattice (stream_id = rank); the
+            units of all ranks over the slowest rank's time (weak scaling);
+  strips    one L = 524288 lattice in row strips, one per rank, with a halo
+            row exchanged with each ring neighbour before every checkerboard
+            step and an int64 all-reduce of the counts at every recorded sweep
+            (the paper's border exchange, Sec. 6.1; strong scaling).
 
 One JSON line on rank 0:
   value          device-timed attempts/ns, lattice resident in HBM
-  e2e            the same through the C ABI from host buffers: each step
-                 creates the lattice from a pinned host copy (H2D), sweeps,
-                 reads the M/E samples back (D2H) and destroys it
+  e2e            the same through the C ABI from pinned host memory: each step
+                 creates the lattice from the host copy (H2D), sweeps, reads
+                 the M/E samples back (D2H) and destroys it
   roofline       the dominant kernel (the half-sweep) against the integer-ALU
-                 bound; achieved = 16 int32 ops per attempt / mean launch time
-  cpu_baseline   the oracle on this host's cores on a bounded strip sample of
-                 the same workload (rank 0, N = 1 only)
+                 bound (16 int32 ops per attempt at 128 lanes per SM per clock),
+                 with the measured draw-generation rates beside it
+  cpu_baseline   the oracle on this host's cores (all, and one) on a bounded
+                 light-cone sample of the same lattice (rank 0, N = 1 only)
+  extras         the L = 32768 lattice, small lattices, the 128-lattice batch,
+                 the served request stream, the field, the paper's shape
 The reference arm (--impl reference) times the oracle itself on that sample.
 """
 from __future__ import annotations
@@ -28,7 +39,7 @@ import argparse
 import hashlib
 import json
 import os
-import re
+import socket
 import statistics
 import subprocess
 import sys
@@ -38,11 +49,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-L = 32768
-T = 2.269185
-SEED = 7
-SWEEPS_PER_STEP = 1000
-WORD_BITS = 32
+L = 524288
+T = 2.0
+SEED = 5
+WORD_BITS = 64
+SWEEPS_PER_STEP = 10
 METRIC = "spin-flip attempts/ns"
 UNIT = "attempts/ns"
 # canonical integer operations per attempt (Philox 10, counter 0.5, compares and
@@ -50,11 +61,12 @@ UNIT = "attempts/ns"
 OPS_PER_ATTEMPT = 16
 INT32_LANES_PER_SM = 128
 CONFIG = {
-    "workload": "L=32768 (2^30 spins, u32 words, 128 MiB), hot start seed 7, T=2.269185, "
-                "1000 sweeps per step, M/E every sweep",
+    "workload": "L=524288 (2^38 spins, u64 words, 32 GiB), cold start, T=2.0, seed 5, "
+                "10 sweeps per step (the 200-sweep run in 20 steps), M/E every sweep",
     "L": L, "T": T, "seed": SEED, "sweeps_per_step": SWEEPS_PER_STEP, "word_bits": WORD_BITS,
     "record_every": 1,
-    "l2": "lattice (128 MiB) read+written twice per sweep; L2 flushed (512 MiB write) between steps",
+    "l2": "no flush: the lattice (32 GiB) is far larger than L2 (129 MB) and is read and "
+          "written twice per sweep",
 }
 
 
@@ -68,6 +80,20 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def free_port() -> int:
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def spawn_ranks(n: int) -> int:
+    """Re-runs this command as n ranks under torch.distributed.run on this node."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(n),
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()), os.path.abspath(__file__)]
+    cmd += sys.argv[1:]
+    return subprocess.call(cmd)
 
 
 # ------------------------------------------------------------------ clocks --
@@ -128,6 +154,7 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- profiles --
 KERNEL_SOURCES = ("kernels.cu", "sweep_device.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "half_sweep_traffic.json")
 
 
 def kernel_source_hash() -> str:
@@ -139,19 +166,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per half-sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "half_sweep_u32_L32768.md")
+def profiled_kernel():
+    """The committed ncu figures of the half-sweep (DRAM bytes per launch at the
+    captured size, thread instructions per attempt), if they were taken on the
+    current kernel source; else None."""
     try:
-        text = open(path).read()
-    except OSError:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
         return None
-    m = re.search(r"sweep_device\.cuh`?\s+sha256\[:16\]:\s*`?([0-9a-f]{16})", text)
-    t = re.search(r"dram bytes per launch:\s*`?([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    if d.get("kernel_sources_sha16") != kernel_source_hash():
         return None
-    return float(t.group(1))
+    return d
 
 
 def measured_peaks():
@@ -163,24 +189,25 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------- CPU oracle ---
-def oracle_strip_sample(target_s: float, max_sweeps: int | None = None):
-    """Time the oracle on a strip of the workload lattice: rows [0, 256) of the
-    L=32768 hot start, light-cone mode, sweeps until about target_s seconds.
-    Returns (attempts, seconds, sweeps, threads)."""
-    import numpy as np  # noqa: F401
+def oracle_window_sample(target_s: float, rows: int = 256, max_sweeps: int | None = None):
+    """Time the oracle on a light-cone window of the workload lattice: rows
+    [0, rows) of the L = 524288 cold start, sweeps until about target_s
+    seconds.  Each sweep counts (rows - 2) x L attempts (the window's edge rows
+    are its fixed boundary).  Returns (attempts, seconds, sweeps, threads)."""
+    import numpy as np
+
     import oracle
 
     oracle.build()
-    rows = 256
     thr4, thr8 = oracle.thresholds(T)
-    s = oracle.init_hot(L, SEED, 0, 0, rows)
+    s = np.ones((rows, L), dtype=np.int8)
     attempts = 0
     sweeps = 0
     t0 = time.perf_counter()
     while True:
         oracle.run_window(s, L, 0, 1, SEED, 0, thr4, thr8, t0=sweeps)
         sweeps += 1
-        attempts += (rows - 2) * L  # the two edge rows of the window are held fixed
+        attempts += (rows - 2) * L
         el = time.perf_counter() - t0
         if el >= target_s or (max_sweeps and sweeps >= max_sweeps):
             break
@@ -188,22 +215,36 @@ def oracle_strip_sample(target_s: float, max_sweeps: int | None = None):
     return attempts, el, sweeps, threads
 
 
-def cpu_baseline(target_s=12.0):
-    a, el, sw, thr = oracle_strip_sample(target_s)
+def oracle_one_core(target_s: float, rows: int = 64):
+    """The same sample on one host thread, in a child process (OMP_NUM_THREADS=1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = ("import json, bench; a, el, sw, thr = bench.oracle_window_sample(%r, rows=%d); "
+            "print(json.dumps([a, el, sw, thr]))" % (target_s, rows))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(target_s=10.0):
+    a, el, sw, thr = oracle_window_sample(target_s)
+    a1, el1, sw1, thr1 = oracle_one_core(target_s)
     return {"value": a / el / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
             "sample": "oracle (one int8 per spin, plain C, OpenMP over rows) on rows 0-255 of the "
-                      "L=32768 hot start, %d sweeps in light-cone mode, %.1f s wall, %d threads"
-                      % (sw, el, thr)}
+                      "L=524288 cold start, %d sweeps in light-cone mode, %.1f s wall, %d threads"
+                      % (sw, el, thr),
+            "one_core": {"value": a1 / el1 / 1e9, "unit": UNIT, "cores": thr1,
+                         "sample": "rows 0-63 of the same lattice, %d sweeps, %.1f s wall, 1 thread"
+                                   % (sw1, el1)}}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        oracle_strip_sample(0.0, max_sweeps=1)
+        oracle_window_sample(0.0, max_sweeps=1)
     total_a, total_t, sweeps, threads = 0, 0.0, 0, 1
     for _ in range(args.steps):
-        a, el, sw, threads = oracle_strip_sample(2.0)
+        a, el, sw, threads = oracle_window_sample(2.0)
         total_a += a
         total_t += el
         sweeps += sw
@@ -214,7 +255,7 @@ def run_reference(args, ws, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8",
         "data": "synthetic", "config": CONFIG, "impl": "reference",
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "each step: oracle on rows 0-255 of the L=32768 hot start "
+                         "sample": "each step: oracle on rows 0-255 of the L=524288 cold start "
                                    "for about 2 s (%d sweeps in total)" % sweeps},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -223,50 +264,128 @@ def run_reference(args, ws, rank):
 
 
 # -------------------------------------------------------------------- ours --
-def extras(P, stream):
-    """Other workloads, on rank 0 at N = 1: the L = 64 lattice (plain launches
-    against one persistent launch), the 128-lattice finite-size-scaling batch
-    (one tuned persistent launch against sequential plain launches) and the
-    L = 32768 lattice in a field."""
-    import numpy as np
+def timed_sweeps(P, lat, stream, sweeps, record_every=1, reps=1):
+    """Device time (CUDA events on the lattice's stream) of `sweeps` sweeps."""
+    import torch
+
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.sweep(sweeps, record_every)
+        e1.record(stream)
+        lat.measure()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best / 1e3
+
+
+def mix_peaks(P, stream):
+    """The integer-mix microbenchmark (ising_bench_mix), draws per ns."""
+    out = {}
+    for form, name in ((0, "full_philox_rounds"), (1, "kernel_philox_form"), (2, "kernel_form_with_masks")):
+        P.ising_bench_mix(form, 2000, stream=stream)
+        best = 0.0
+        for _ in range(2):
+            _, r = P.ising_bench_mix(form, 40000, stream=stream)
+            best = max(best, r)
+        out[name] = best
+    return out
+
+
+def served_extras(P):
+    """The served stream, shortened: an overload stream (200 requests/s for 10 s,
+    then up to 40 s to drain) and a stream at 60 % of the capacity the overload
+    run measured; and the first 120 requests of the stream served together
+    against the same requests run one after another with plain launches."""
+    from paper_1007_3726_gb300 import serve
+
+    out = {}
+    reqs = serve.poisson_requests(rate=200.0, duration=10.0, seed=4)
+    with P.Server(hbm_budget_bytes=64 * 10 ** 9, epoch_sweeps=1000) as srv:
+        over = serve.run_stream(srv, reqs, drain_s=40.0)
+    out["overload_200_per_s_10s"] = over
+    mean_work = sum(r["L"] ** 2 * r["nsweeps"] for r in reqs) / len(reqs)
+    cap = over["server_attempts_per_ns"] * 1e9  # attempts per second
+    rate = 0.6 * cap / mean_work
+    reqs60 = serve.poisson_requests(rate=rate, duration=20.0, seed=4)
+    with P.Server(hbm_budget_bytes=64 * 10 ** 9, epoch_sweeps=1000) as srv:
+        r60 = serve.run_stream(srv, reqs60, drain_s=40.0)
+    r60["offered_rate_per_s"] = rate
+    r60["offered_attempts_per_ns"] = rate * mean_work / 1e9
+    out["at_60pct_of_capacity"] = r60
+    # the same requests served together vs sequential plain launches
+    same = [dict(r, t=0.0) for r in reqs[:120]]
+    work = sum(r["L"] ** 2 * r["nsweeps"] for r in same)
+    with P.Server(hbm_budget_bytes=64 * 10 ** 9, epoch_sweeps=1000) as srv:
+        t = time.perf_counter()
+        s = serve.run_stream(srv, same, drain_s=600.0)
+        t_served = time.perf_counter() - t
+    t = time.perf_counter()
+    for r in same:
+        with P.Lattice(r["L"], r["T"], seed=r["seed"], init="hot") as lat:
+            lat.sweep(r["nsweeps"], r["record_every"])
+            lat.measure()
+    t_seq = time.perf_counter() - t
+    out["same_120_requests"] = {
+        "served_attempts_per_ns": work / t_served / 1e9, "sequential_plain_attempts_per_ns": work / t_seq / 1e9,
+        "served_over_sequential": t_seq / t_served, "completed": s["completed"],
+        "note": "all 120 submitted at once; sequential: one Lattice per request, ising_sweep's default "
+                "launch, in submission order"}
+    return out
+
+
+def extras(P, stream, peaks, mix):
+    """Other workloads, on rank 0 at N = 1."""
     import torch
 
     from paper_1007_3726_gb300 import workloads as WL
 
     out = {}
-    w = WL.plain_L64()
+    # the L = 32768 lattice (hot start, T = T_c): 1000 sweeps, device-timed
+    w = WL.large_L32768()
+    lat = P.Lattice(**WL.lattice_kwargs(w), stream=stream)
+    cfg, _ = lat.autotune(reps=3)
+    timed_sweeps(P, lat, stream, 20)
+    t = timed_sweeps(P, lat, stream, w["sweeps"], reps=2)
+    rate = w["L"] ** 2 * w["sweeps"] / t / 1e9
+    mean_launch = t / (2 * w["sweeps"])
+    out["L32768_1000_sweeps"] = {
+        "attempts_per_ns": rate, "launch": cfg, "mean_launch_us": mean_launch * 1e6,
+        "frac_nominal_int32": OPS_PER_ATTEMPT * rate * 1e9 / (peaks["int32_tops"] * 1e12),
+        "frac_of_measured_draw_rate": rate / mix["kernel_philox_form"],
+        "frac_of_measured_draws_with_masks": rate / mix["kernel_form_with_masks"],
+        "note": "the previous headline workload: 2^30 spins, u32 storage, hot start seed 7, T=2.269185, "
+                "M/E every sweep; best of 2 device-timed 1000-sweep runs"}
+    lat.close()
 
-    def timed_call(lat):
+    def wall_call(lat, sweeps):
         lat.sweep(20, 1)
         lat.measure()
         t = time.perf_counter()
-        lat.sweep(w["sweeps"], 1)
+        lat.sweep(sweeps, 1)
         lat.measure()
         return time.perf_counter() - t
 
-    a = P.Lattice(**WL.lattice_kwargs(w))            # default: the one-CTA kernel
-    t_cta = timed_call(a)
-    s = P.Lattice(**WL.lattice_kwargs(w))
-    s.set_launch(proc_bits=32, regcap=0, insert=0, block=128, rows_per_item=4, grid=0)
-    t_steps = timed_call(s)
-    b_lat = P.Lattice(**WL.lattice_kwargs(w))
-    with P.Batch([b_lat], [w["sweeps"]], 1) as b:
-        b.run(1)
-        t = time.perf_counter()
-        b.run(1)
-        t_batch = time.perf_counter() - t
-    n64 = 64 * 64 * w["sweeps"]
-    out["L64_1000_sweeps"] = {"one_cta_attempts_per_ns": n64 / t_cta / 1e9,
-                              "step_launches_attempts_per_ns": n64 / t_steps / 1e9,
-                              "batch_attempts_per_ns": n64 / t_batch / 1e9,
-                              "one_sm_bound_attempts_per_ns": 40.27e12 / 152 / 16 / 1e9,
-                              "launch": a.launch,
-                              "note": "wall time of one call (launch, 1000 sweeps, read-back of 1000 "
-                                      "M/E samples); one CTA: ising_sweep's default at this size; step "
-                                      "launches: 2 kernels per sweep; batch: the persistent batch kernel"}
-    for x in (a, s, b_lat):
-        x.close()
+    # small lattices: one CTA (L = 64) and an 8-CTA cluster (L = 256)
+    for Ls, name in ((64, "L64_1000_sweeps"), (256, "L256_1000_sweeps")):
+        a = P.Lattice(Ls, 2.269185, seed=1, init="cold_up")
+        ta = min(wall_call(a, 1000) for _ in range(3))
+        n = Ls * Ls * 1000
+        d = {"attempts_per_ns": n / ta / 1e9, "launch": a.launch,
+             "note": "wall time of one ising_sweep call (launch, 1000 sweeps, read-back of 1000 M/E samples), "
+                     "best of 3"}
+        s = P.Lattice(Ls, 2.269185, seed=1, init="cold_up")
+        s.set_launch(proc_bits=32, regcap=0, insert=0, block=128, rows_per_item=4, grid=0)
+        d["step_launches_attempts_per_ns"] = n / wall_call(s, 1000) / 1e9
+        ctas = max(1, a.launch["grid"])
+        d["issue_bound_attempts_per_ns"] = ctas * INT32_LANES_PER_SM * peaks["sm_max_ghz"] / OPS_PER_ATTEMPT
+        out[name] = d
+        a.close()
+        s.close()
 
+    # the 128-lattice finite-size-scaling batch: one tuned persistent launch
     specs = WL.fss_batch()
     lats = [P.Lattice(**WL.lattice_kwargs(sp)) for sp in specs]
     sweeps = [sp["sweeps"] for sp in specs]
@@ -278,19 +397,6 @@ def extras(P, stream):
         t = time.perf_counter()
         b.run(1)
         t_b = time.perf_counter() - t
-    # U4 per (L, T) with 20 % burn-in, and where the L=256 and L=512 curves cross
-    u4 = {}
-    nsamp = sweeps[0] // specs[0]["record_every"]
-    for sp, lat in zip(specs, lats):
-        d = lat.measure(first_sample=nsamp // 5)
-        u4.setdefault(sp["L"], []).append(d["U4"])
-    temps = WL.fss_temperatures()
-    cross = []
-    diff = np.array(u4[512]) - np.array(u4[256])
-    for i in range(len(temps) - 1):
-        if diff[i] > 0 >= diff[i + 1] or diff[i] < 0 <= diff[i + 1]:
-            cross.append(temps[i] + (temps[i + 1] - temps[i]) * diff[i] / (diff[i] - diff[i + 1]))
-    # sequential plain launches on the same lattices, 200 sweeps each
     t = time.perf_counter()
     for lat in lats:
         lat.sweep(200, 10)
@@ -301,21 +407,14 @@ def extras(P, stream):
         "persistent_attempts_per_ns": N * sweeps[0] / t_b / 1e9,
         "sequential_plain_attempts_per_ns": N * 200 / t_p / 1e9,
         "seconds": t_b, "plan": info, "options": opts,
-        "U4_crossings_L256_L512": cross,
-        "U4_burn_in": "first 20 % of the samples dropped",
         "note": "10^4 sweeps of 128 lattices in one launch (wall time incl. sample read-back); "
-                "plain: 2 launches per sweep per lattice, 200 sweeps each"}
+                "plain: each lattice's default launch, 200 sweeps each, one after another"}
     for lat in lats:
         lat.close()
 
-    # the same L = 32768 lattice in a field H = 0.1 (ten acceptance classes)
+    # the L = 32768 lattice in a field H = 0.1 (ten acceptance classes)
     f = P.Lattice(32768, 2.269185, seed=7, init="hot", H=0.1)
-    f.sweep(10, 1)
-    f.measure()
-    t = time.perf_counter()
-    f.sweep(200, 1)
-    f.measure()
-    t_f = time.perf_counter() - t
+    t_f = wall_call(f, 200)
     out["field_L32768_H0.1"] = {"attempts_per_ns": 32768 ** 2 * 200 / t_f / 1e9,
                                 "note": "200 sweeps, M/E every sweep, wall time of one call"}
     f.close()
@@ -324,72 +423,210 @@ def extras(P, stream):
     w = WL.paper_benchmark()
     q = P.Lattice(**WL.lattice_kwargs(w))
     q.autotune(reps=2)
-    t_q = timed_call(q)
+    t_q = wall_call(q, w["sweeps"])
     out["paper_shape_L4096_0.99Tc"] = {
         "attempts_per_ns": 4096 ** 2 * w["sweeps"] / t_q / 1e9, "launch": q.launch,
         "note": "1000 sweeps, M/E every sweep, wall time of one call; the paper's best single-GPU "
                 "figure on this shape is 7.98 attempts/ns (Tesla C1060, another RNG): context only"}
     q.close()
+
+    out["served"] = served_extras(P)
     return out
 
 
-def run_largest(args):
-    """The largest single-GPU lattice: L = 524288 (2^38 spins, 32 GiB), cold start,
-    T = 2.0, 200 sweeps, M/E every sweep; one JSON line with attempts/ns and the
-    magnetisation per spin against Onsager's m0(2.0)."""
+class StripsRun:
+    """The workload lattice as row strips over the ranks (NCCL halo exchange)."""
+
+    def __init__(self, P, ws, rank, stream):
+        from paper_1007_3726_gb300.distributed import StripLattice, TorchDistExchange
+
+        self.strip = StripLattice(L, T, seed=SEED, init="cold_up", rank=rank, world=ws, word_bits=WORD_BITS)
+        self.ex = TorchDistExchange()
+
+    def sweep(self, n, record_every):
+        from paper_1007_3726_gb300.distributed import sweep_strips
+
+        return sweep_strips([self.strip], self.ex, L, n, record_every)
+
+    def close(self):
+        self.strip = None
+
+
+def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
 
     import paper_1007_3726_gb300 as P
-    from paper_1007_3726_gb300 import workloads as WL
 
-    w = WL.largest_L524288()
-    lat = P.Lattice(**WL.lattice_kwargs(w))
-    cfg, _ = lat.autotune(reps=1)
-    lat.sweep(2, 1)
-    lat.measure()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    P.load()
+    stream = torch.cuda.Stream(device=dev)
+    N = L * L
+    strips = args.parallelism == "strips" and ws > 1
+    units_per_step = N * SWEEPS_PER_STEP * (1 if strips else ws)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------- device-resident timing
+    tuned, tuned_us = None, None
+    if strips:
+        with torch.cuda.stream(stream):
+            lat = StripsRun(P, ws, rank, stream)
+    else:
+        lat = P.Lattice(L, T, seed=SEED, stream_id=rank, init="cold_up", word_bits=WORD_BITS, stream=stream)
+        tuned, tuned_us = lat.autotune(reps=2)   # launch shape only: results are identical
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lat.sweep(SWEEPS_PER_STEP, 1)
+            if not strips:
+                lat.measure()
     torch.cuda.synchronize()
-    t = time.perf_counter()
-    M, E = lat.sweep(w["sweeps"] - 2, 1, collect=True)
-    el = time.perf_counter() - t
-    N = float(w["L"]) ** 2
-    m = float(np.mean(np.abs(M[98:]) / N))
-    line = {"metric": METRIC, "value": N * (w["sweeps"] - 2) / el / 1e9, "unit": UNIT, "n_gpus": 1,
-            "steps": 1, "warmup": 1, "ms_per_step": el * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "L=524288 (2^38 spins, u64 words, 32 GiB), cold start, T=2.0, "
-                                   "seed 5, 198 timed sweeps, M/E every sweep", "launch": cfg},
-            "mean_abs_m_sweeps_100_200": m, "onsager_m0": WL.onsager_m0(2.0),
-            "e_last": float(E[-1]) / N}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            ev[i][0].record(stream)
+            lat.sweep(SWEEPS_PER_STEP, 1)   # 2 half-sweep launches per sweep
+            ev[i][1].record(stream)
+        if not strips:
+            lat.measure()                   # harvests the samples, FP64 moments on the host
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = max_over_ranks(sum(step_ms) / 1e3)
+    value = units_per_step * args.steps / t_dev / 1e9
+    obs = None if strips else lat.measure()
+    lat.close()
+    launches = 2 * SWEEPS_PER_STEP * args.steps
+    mean_launch_s = sum(step_ms) / 1e3 / launches
+
+    # ---------------- end to end through the C ABI from pinned host memory
+    nbytes = N // 8
+    e2e_value, h2d, d2h = None, 0, 0
+    if not strips:
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        host.fill_(0xFF)                                  # the cold start, packed
+        hp = host.numpy().view(np.uint64).reshape(L, L // 64)
+        Mh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
+        Eh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
+
+        def e2e_step():
+            lt = P.Lattice(L, T, seed=SEED, stream_id=rank, packed=hp, word_bits=WORD_BITS, stream=stream)
+            P.ising_sweep(lt.handle, SWEEPS_PER_STEP, 1, Mh, Eh, SWEEPS_PER_STEP)
+            lt.close()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e_value = units_per_step * args.steps / t_e2e / 1e9
+        h2d, d2h = nbytes, int(Mh.nbytes + Eh.nbytes)
+        del host
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+    peak_tops = sms * INT32_LANES_PER_SM * sm_max_ghz * 1e9 / 1e12
+    per_rank_attempts = N / 2 / (ws if strips else 1)
+    achieved_tops = OPS_PER_ATTEMPT * per_rank_attempts / mean_launch_s / 1e12
+    rate_per_gpu = per_rank_attempts / mean_launch_s / 1e9  # attempts/ns of one GPU's launches
+    mix = mix_peaks(P, stream) if ws == 1 else None
+    prof = profiled_kernel()
+    traffic = None
+    if prof and not strips:
+        # DRAM bytes of one launch at the captured size, scaled by the sites of this one
+        traffic = prof["dram_bytes_per_launch"] * (N / float(prof["L"]) ** 2)
+    roof = {
+        "bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
+        "frac": achieved_tops / peak_tops, "traffic": traffic,
+        "kernel": "k_half_sweep (proc_bits=%s, regcap=%s)" % (
+            tuned["proc_bits"] if tuned else "default", tuned["regcap"] if tuned else "default"),
+        "peak_basis": "%d SMs x %d int32 lanes x %.2f GHz (max SM clock), derived" % (
+            sms, INT32_LANES_PER_SM, sm_max_ghz),
+        "achieved_basis": "%d ops/attempt x %d attempts per launch / mean launch time %.1f us (CUDA events "
+                          "over the timed region)" % (OPS_PER_ATTEMPT, per_rank_attempts, mean_launch_s * 1e6),
+        "hbm_view": {"bytes_per_launch_algorithmic": per_rank_attempts * 2 / 8 * 2,
+                     "achieved_gbs": per_rank_attempts * 2 / 8 * 2 / mean_launch_s / 1e9,
+                     "peak_gbs": peaks.get("hbm_gbs"), "peak_note": "of measured"},
+    }
+    if traffic is not None:
+        roof["traffic_basis"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at L=%d, "
+                                 "scaled by the sites per launch (%s)" % (prof["L"], prof["source"]))
+        roof["ncu_thread_instructions_per_attempt"] = prof.get("thread_inst_per_attempt")
+    if mix:
+        roof["measured_mix"] = dict(mix, unit="draws/ns", how="ising_bench_mix: one wave of resident 512-thread "
+                                    "blocks, 32 draws per thread per word, CUDA events",
+                                    frac_of_kernel_philox_form=rate_per_gpu / mix["kernel_philox_form"],
+                                    frac_of_kernel_form_with_masks=rate_per_gpu / mix["kernel_form_with_masks"],
+                                    peak_tops_equivalent=OPS_PER_ATTEMPT * mix["kernel_philox_form"] / 1e3,
+                                    frac_of_peak_tops_equivalent=achieved_tops / (
+                                        OPS_PER_ATTEMPT * mix["kernel_philox_form"] / 1e3))
+    config = dict(CONFIG, parallelism=("strips" if strips else "replicas") if ws > 1 else "single")
+    if strips:
+        config["workload"] += "; one lattice in %d row strips, NCCL halo exchange" % ws
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "strong" if strips else "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic", "config": config,
+        "roofline": roof,
+        "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "how": "per step: ising_create from the pinned packed cold start (H2D), ising_sweep of 10 "
+                        "sweeps returning the 10 M/E samples (D2H), ising_destroy"}
+                if e2e_value is not None else None),
+        "gpu_launches": launches,
+        "launch": dict(tuned, autotune_us_per_step=tuned_us) if tuned else None,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if obs is not None:
+        line["observables_last_step"] = {"mean_abs_m": obs["mean_abs_m"], "mean_e": obs["mean_e"],
+                                         "n_samples": obs["n_samples"]}
+    if ws == 1 and not args.no_extras:
+        line["extras"] = extras(P, stream, {"int32_tops": peak_tops, "sm_max_ghz": sm_max_ghz}, mix)
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
-    return 0
+    if ws > 1:
+        import torch.distributed as dist
 
-
-def run_served(args):
-    """The served request stream: Poisson arrivals at 200 requests/s for 60 s (L
-    uniform on the powers of two 64..4096, T uniform in [1.5, 3.5], sweeps
-    log-uniform in [10^2, 10^5], per-request seeds), admitted against a 64 GB
-    budget, then 60 s to drain; and a sustainable-rate stream at 20 requests/s.
-    One JSON line with p50/p99 latency and aggregate attempts/ns."""
-    import paper_1007_3726_gb300 as P
-    from paper_1007_3726_gb300 import serve
-
-    runs = {}
-    for name, rate, dur, drain in (("offered_200_per_s", 200.0, 60.0, 60.0),
-                                   ("sustainable_20_per_s", 20.0, 60.0, 120.0)):
-        reqs = serve.poisson_requests(rate=rate, duration=dur, seed=4)
-        with P.Server(hbm_budget_bytes=64 * 10 ** 9, epoch_sweeps=1000) as srv:
-            runs[name] = serve.run_stream(srv, reqs, drain_s=drain)
-    main = runs["offered_200_per_s"]
-    line = {"metric": "served p50/p99 latency and aggregate spin-flip attempts/ns",
-            "value": main["server_attempts_per_ns"], "unit": UNIT, "n_gpus": 1, "steps": 1,
-            "warmup": 0, "ms_per_step": main["makespan_s"] * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "Poisson 200 req/s for 60 s, L in 64..4096 (powers of two), "
-                                   "T in [1.5, 3.5], sweeps log-uniform 1e2..1e5, budget 64 GB, "
-                                   "M/E every 10 sweeps, 60 s drain"},
-            "runs": runs}
-    print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
     return 0
 
 
@@ -433,178 +670,33 @@ def run_fss(args):
     return 0
 
 
-def run_ours(args, ws, rank, local):
-    import numpy as np
-    import torch
-
-    import paper_1007_3726_gb300 as P
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
-    P.load()
-    stream = torch.cuda.Stream(device=dev)
-    N = L * L
-    units_per_step = N * SWEEPS_PER_STEP
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-
-    # ---------------- device-resident timing
-    lat = P.Lattice(L, T, seed=SEED, stream_id=rank, init="hot", word_bits=WORD_BITS, stream=stream)
-    tuned, tuned_us = lat.autotune(reps=3)   # launch shape only: results are identical
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            lat.sweep(SWEEPS_PER_STEP, 1)
-            lat.measure()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    barrier()
-    clocks.start()
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(i & 0xFF)           # evict the lattice from L2 between steps
-            ev[i][0].record(stream)
-            lat.sweep(SWEEPS_PER_STEP, 1)   # 2 half-sweep launches per sweep
-            ev[i][1].record(stream)
-        lat.measure()                       # harvests the samples, FP64 moments on the host
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_dev = max_over_ranks(sum(step_ms) / 1e3)
-    value = units_per_step * args.steps * ws / t_dev / 1e9
-    obs = lat.measure()
-    lat.close()
-    launches = 2 * SWEEPS_PER_STEP * args.steps
-    mean_launch_s = sum(step_ms) / 1e3 / launches
-
-    # ---------------- end to end through the C ABI from host buffers
-    src = P.Lattice(L, T, seed=SEED, stream_id=rank, init="hot", word_bits=WORD_BITS, stream=stream)
-    packed = src.packed()
-    src.close()
-    host = torch.from_numpy(packed).pin_memory()
-    hp = host.numpy()
-    Mh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
-    Eh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
-
-    def e2e_step():
-        lt = P.Lattice(L, T, seed=SEED, stream_id=rank, packed=hp, word_bits=WORD_BITS,
-                       stream=stream)
-        P.ising_sweep(lt.handle, SWEEPS_PER_STEP, 1, Mh, Eh, SWEEPS_PER_STEP)
-        d = lt.measure()
-        lt.close()
-        return d
-
-    for _ in range(max(1, min(args.warmup, 2))):
-        e2e_step()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        e2e_step()
-    torch.cuda.synchronize()
-    t_e2e_wall = time.perf_counter() - t0
-    t_e2e = max_over_ranks(t_e2e_wall)
-    e2e_value = units_per_step * args.steps * ws / t_e2e / 1e9
-
-    if rank != 0:
-        if ws > 1:
-            import torch.distributed as dist
-
-            dist.destroy_process_group()
-        return 0
-
-    peaks = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    sm_max_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
-    peak_tops = sms * INT32_LANES_PER_SM * sm_max_ghz * 1e9 / 1e12
-    achieved_tops = OPS_PER_ATTEMPT * (N / 2) / mean_launch_s / 1e12
-    traffic = profiled_traffic()
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_dev * 1e3 / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "config": dict(CONFIG, parallelism="replicas" if ws > 1 else "single"),
-        "roofline": {
-            "bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (int32)",
-            "frac": achieved_tops / peak_tops, "traffic": traffic,
-            "kernel": "k_half_sweep (proc_bits=%d, regcap=%d)" % (tuned["proc_bits"], tuned["regcap"]),
-            "peak_basis": "%d SMs x %d int32 lanes x %.2f GHz (max SM clock)" % (
-                sms, INT32_LANES_PER_SM, sm_max_ghz),
-            "achieved_basis": "%d ops/attempt x N/2 attempts per launch / mean launch time %.1f us"
-                              % (OPS_PER_ATTEMPT, mean_launch_s * 1e6),
-            "hbm_view": {"bytes_per_launch_algorithmic": N / 8 * 2,
-                         "achieved_gbs": N / 8 * 2 / mean_launch_s / 1e9,
-                         "peak_gbs": peaks.get("hbm_gbs"), "peak_note": "of measured"},
-        },
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(packed.nbytes),
-                "d2h_bytes_per_step": int(Mh.nbytes + Eh.nbytes)},
-        "gpu_launches": launches,
-        "launch": dict(tuned, autotune_us_per_step=tuned_us),
-        "clocks": clk,
-        "wall_s_timed": wall,
-        "observables_last_step": {"U4": obs["U4"], "mean_abs_m": obs["mean_abs_m"],
-                                  "mean_e": obs["mean_e"], "n_samples": obs["n_samples"]},
-    }
-    if ws == 1 and not args.no_extras:
-        line["extras"] = extras(P, stream)
-    if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.destroy_process_group()
-    return 0
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--parallelism", choices=["replicas", "strips"], default="replicas",
+                    help="N > 1: a lattice per rank (replicas) or one lattice in row strips (strips)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the L=64 and 128-lattice workloads")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     ap.add_argument("--fss-sweeps", type=int, default=200000)
     ap.add_argument("--fss-long", action="store_true",
                     help="--workload fss on L = 64, 128, 256 with sweeps ~ L^2.17 (2e5 at L = 64) "
                          "on 16 T in [2.255, 2.285]")
-    ap.add_argument("--workload", default="default", choices=["default", "largest", "served", "fss"],
-                    help="default: L=32768 (the benchmark line); largest: L=524288; served: request stream")
+    ap.add_argument("--workload", default="default", choices=["default", "fss"],
+                    help="default: the L=524288 line; fss: the U4 crossings")
     args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("--steps must be >= 1 and --warmup >= 0")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        return spawn_ranks(args.gpus)
     ws, rank, local = dist_setup()
+    if ws != args.gpus:
+        print("bench.py: WORLD_SIZE=%d but --gpus %d" % (ws, args.gpus), file=sys.stderr)
+        return 2
     if args.impl == "reference":
         return run_reference(args, ws, rank)
-    if args.workload == "largest":
-        return run_largest(args)
-    if args.workload == "served":
-        return run_served(args)
     if args.workload == "fss":
         return run_fss(args)
     return run_ours(args, ws, rank, local)

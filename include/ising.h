@@ -426,6 +426,14 @@ ISING_API ising_status ising_strip_step(void *d_rows, uint64_t L, uint32_t word_
                                         uint64_t nrows, double T, uint64_t seed, uint32_t stream_id, uint32_t t,
                                         uint32_t p, unsigned long long *d_counts, void *cuda_stream);
 
+/* M and E (Sec. 3, Eq. 1 with J = 1, H = 0) of a whole L x L lattice from the
+ * summed step-B counts of its strips: n_up spins +1 and n_anti anti-aligned
+ * bonds (of the 2 L^2) give M = 2 n_up - L^2 and E = 2 n_anti - 2 L^2.
+ * Any L in [2, 2^20] (the counts may come from strips stepped elsewhere);
+ * ISING_ERR_INVALID for null outputs, such an L or counts beyond the lattice. */
+ISING_API ising_status ising_strip_observables(uint64_t L, uint64_t n_up, uint64_t n_anti, int64_t *M,
+                                               int64_t *E);
+
 /*
  * ising_sweep_noalloc - the sweep for callers that cannot allocate memory.
  * The paper has no counterpart; this entry point exists for callers that own

@@ -22,7 +22,7 @@ __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
     "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount", "ising_get_samples",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
-    "ising_device_spins", "ising_sweep_noalloc", "ising_bench_mix", "ising_strip_init", "ising_strip_step", "ising_get_launch", "ising_set_launch",
+    "ising_device_spins", "ising_sweep_noalloc", "ising_bench_mix", "ising_strip_init", "ising_strip_step", "ising_strip_observables", "ising_get_launch", "ising_set_launch",
     "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "Server", "IsingBatchOpts",
     "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
@@ -178,6 +178,8 @@ def load(path: str | None = None):
         "ising_set_field": ([H, ctypes.c_double], ctypes.c_int),
         "ising_get_params": ([H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                              ctypes.c_int),
+        "ising_strip_observables": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _i64p, _i64p],
+                                    ctypes.c_int),
         "ising_bench_mix": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
         "ising_sweep_noalloc": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
@@ -499,6 +501,14 @@ def ising_strip_step(d_rows: int, L: int, word_bits: int, row0: int, nrows: int,
                      stream_id: int, t: int, p: int, d_counts: int | None = None, stream=None):
     _check(load().ising_strip_step(d_rows, L, word_bits, row0, nrows, float(T), seed, stream_id, t, p,
                                    d_counts, _stream_ptr(stream)))
+
+
+def ising_strip_observables(L: int, n_up: int, n_anti: int) -> tuple[int, int]:
+    """(M, E) of an L x L lattice from its summed step-B counts (see include/ising.h)."""
+    M = ctypes.c_int64()
+    E = ctypes.c_int64()
+    _check(load().ising_strip_observables(L, n_up, n_anti, ctypes.byref(M), ctypes.byref(E)))
+    return M.value, E.value
 
 
 _alloc_keepalive = []

@@ -92,4 +92,18 @@ ISING_API ising_status ising_strip_step(void *d_rows, uint64_t L, uint32_t word_
     return ISING_OK;
 }
 
+ISING_API ising_status ising_strip_observables(uint64_t L, uint64_t n_up, uint64_t n_anti, int64_t *M, int64_t *E)
+{
+    clear_error();
+    if (!M || !E) return fail(ISING_ERR_INVALID, "null output");
+    // any lattice size: the strips may come from another implementation of the step
+    if (L < 2 || L > (1ull << 20)) return fail(ISING_ERR_INVALID, "L must be in [2, 2^20]");
+    const uint64_t N = L * L;
+    if (n_up > N || n_anti > 2 * N) return fail(ISING_ERR_INVALID, "counts exceed the lattice");
+    // M = (+1 spins) - (-1 spins); E = -(aligned bonds) + (anti-aligned bonds), 2N bonds
+    *M = 2 * (int64_t)n_up - (int64_t)N;
+    *E = 2 * (int64_t)n_anti - 2 * (int64_t)N;
+    return ISING_OK;
+}
+
 }  // extern "C"

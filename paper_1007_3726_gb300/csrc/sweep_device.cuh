@@ -372,6 +372,46 @@ __device__ __forceinline__ Word update_word(const K &a, const S &s, Word cur, Wo
     return nw;
 }
 
+// The update of update_word with the acceptance masks drawn beforehand (the
+// one-CTA kernels draw several steps ahead): pk holds this thread's masks in
+// one word, P4 at the even and P8 at the odd bit positions of the word's
+// target bytes (pack_masks), independent of the parity off.
+__device__ __forceinline__ uint32_t pack_masks(uint32_t p4, uint32_t p8) { return p4 | (p8 << 1); }
+
+template <int NQ>
+__device__ __forceinline__ uint32_t update_word32_drawn(uint32_t cur, uint32_t up, uint32_t dn, uint32_t lw,
+                                                        uint32_t rw, uint32_t off, uint32_t pk, bool count,
+                                                        unsigned int &cnt_up, unsigned int &cnt_anti,
+                                                        uint32_t q0)
+{
+    constexpr uint32_t even = 0x55555555u;
+    const uint32_t left = (cur << 1) | (lw >> 31);
+    const uint32_t right = (cur >> 1) | (rw << 31);
+    const uint32_t mask = off ? (even << 1) : even;
+    const uint32_t i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
+    const uint32_t s12 = i1 ^ i2, c12 = i1 & i2;
+    const uint32_t s34 = i3 ^ i4, c34 = i3 & i4;
+    const uint32_t odd = s12 ^ s34;
+    const uint32_t ge2 = c12 | c34 | (s12 & s34);
+    const uint32_t eq1 = odd & ~ge2;
+    const uint32_t eq0 = ~(odd | ge2);
+    const uint32_t p4 = (pk & even) << off;
+    const uint32_t p8 = ((pk >> 1) & even) << off;
+    uint32_t sel = mask;
+    uint32_t own = ~0u;
+    if constexpr (NQ < 4) {
+        own = ((1u << (8 * NQ)) - 1u) << (8 * q0);
+        sel &= own;
+    }
+    const uint32_t nw = cur ^ (sel & (ge2 | (eq1 & p4) | (eq0 & p8)));
+    if (count) {
+        cnt_up += __popc(nw & own);
+        cnt_anti += __popc(sel & (nw ^ up)) + __popc(sel & (nw ^ dn)) + __popc(sel & (nw ^ left)) +
+                    __popc(sel & (nw ^ right));
+    }
+    return nw;
+}
+
 // The items of one checkerboard step of the step kernel's geometry and launch
 // constants (a: the lattice buffer, rows, words per row, rows per item, grid
 // stride, keys, thresholds) with the step values sa (as above: the step-uniform

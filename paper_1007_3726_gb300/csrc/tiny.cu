@@ -26,6 +26,51 @@ namespace {
 
 constexpr uint32_t kTinyMaxThreads = 512;
 
+// Sweeps whose acceptance masks a thread draws in one burst when it holds a
+// single word (the draw-ahead path below): 4 sweeps, 8 checkerboard steps.
+constexpr uint32_t kAheadSweeps = 4;
+
+// The step-uniform Philox values of sweep t, parity p (as prepare_half_sweep).
+__device__ __forceinline__ void tiny_step_values(HalfSweepArgs &a, const TinyRunArgs &A, uint32_t t, uint32_t p)
+{
+    const uint64_t pb = (uint64_t)t * kPhiloxMulB;
+    a.r1x0 = (uint32_t)(pb >> 32) ^ A.key.k0[0];
+    a.r2x0k = (uint32_t)pb ^ A.key.k0[1];
+    const uint64_t pa = (uint64_t)a.r1x0 * kPhiloxMulA;
+    a.r2x2k = (uint32_t)(pa >> 32) ^ A.key.k1[1];
+    a.r2x3 = (uint32_t)pa;
+    a.r1x2k = (A.c3base | p) ^ A.key.k1[0];
+}
+
+// The masks of this thread's bytes of its word (first Philox group g) for the
+// 2 ns steps of sweeps t .. t + ns - 1, packed as pack_masks does.
+template <int NQ>
+__device__ __forceinline__ void tiny_draw_ahead(HalfSweepArgs &a, const TinyRunArgs &A, uint32_t t, uint32_t ns,
+                                                uint64_t g, uint32_t q0, uint32_t (&pk)[2 * kAheadSweeps])
+{
+#pragma unroll
+    for (uint32_t j = 0; j < 2 * kAheadSweeps; ++j) {
+        if (j < 2 * ns) {
+            tiny_step_values(a, A, t + (j >> 1), j & 1u);
+            uint32_t h4[1], h8[1];
+            word_draw_masks<4, 0, NQ>(a, a, g, h4, h8, q0);
+            pk[j] = pack_masks(h4[0], h8[0]);
+        }
+    }
+}
+
+// Stores this thread's bytes of a new word.
+template <int NQ>
+__device__ __forceinline__ void tiny_store(uint32_t *word, uint32_t nw, uint32_t sub)
+{
+    if (NQ == 4)
+        *word = nw;
+    else if (NQ == 2)
+        reinterpret_cast<uint16_t *>(word)[sub] = (uint16_t)(nw >> (16 * sub));
+    else
+        reinterpret_cast<uint8_t *>(word)[sub] = (uint8_t)(nw >> (8 * sub));
+}
+
 template <int NQ, bool FIELD>  // Philox calls (bytes) per thread: 4, 2 or 1; field update
 __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant__ TinyRunArgs A)
 {
@@ -54,6 +99,69 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
     a.zero = 0u;
     uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;  // t % record_every
     uint32_t slot = 0;
+    if (!FIELD && nwords * S <= nthr) {
+        // Draw-ahead path: every thread holds at most one word (or its share of
+        // one).  The draws do not depend on the spins, so each thread draws the
+        // masks of its word for the next kAheadSweeps sweeps in one burst (many
+        // independent Philox chains), then every step is the bit logic, a
+        // store and the barrier.
+        const bool active = tid < nwords * S;
+        const uint32_t k = active ? tid / S : 0u, sub = tid % S;
+        const uint32_t y = k >> lgW, w = k & (W - 1u);
+        const uint32_t row = k - w;
+        const uint32_t iu = (y == 0 ? nwords - W : row - W) + w, id = (y + 1 == L ? 0u : row + W) + w;
+        const uint32_t il = row + ((w - 1u) & (W - 1u)), ir = row + ((w + 1u) & (W - 1u));
+        const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
+        for (uint32_t i0 = 0; i0 < A.nsweeps; i0 += kAheadSweeps) {
+            const uint32_t ns = min(kAheadSweeps, A.nsweeps - i0);
+            uint32_t pk[2 * kAheadSweeps];
+            if (active) tiny_draw_ahead<NQ>(a, A, A.t0 + i0, ns, g, sub * NQ, pk);
+#pragma unroll
+            for (uint32_t j = 0; j < 2 * kAheadSweeps; ++j) {
+                if (j >= 2 * ns) break;
+                const uint32_t p = j & 1u;
+                const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
+                const bool last = i0 + (j >> 1) + 1 == A.nsweeps;
+                const bool count = p == 1u && (rec || last);
+                unsigned int cu = 0, ca = 0;
+                if (active) {
+                    const uint32_t nw = update_word32_drawn<NQ>(lat[k], lat[iu], lat[id], lat[il], lat[ir],
+                                                                (y + p) & 1u, pk[j], count, cu, ca, sub * NQ);
+                    tiny_store<NQ>(lat + k, nw, sub);
+                }
+                if (count) {
+                    cu = __reduce_add_sync(0xFFFFFFFFu, cu);
+                    ca = __reduce_add_sync(0xFFFFFFFFu, ca);
+                    if ((tid & 31u) == 0) {
+                        atomicAdd(&cnt[0], cu);
+                        atomicAdd(&cnt[1], ca);
+                    }
+                }
+                __syncthreads();
+                if (count && tid == 0) {
+                    const unsigned long long c0 = cnt[0], c1 = cnt[1];
+                    if (rec) {
+                        A.acc[2 * slot] = c0;
+                        A.acc[2 * slot + 1] = c1;
+                    }
+                    if (last) {
+                        A.acc[2 * A.nrec] = c0;
+                        A.acc[2 * A.nrec + 1] = c1;
+                    }
+                    cnt[0] = 0u;
+                    cnt[1] = 0u;
+                }
+                if (p == 1u) {
+                    if (rec) ++slot;
+                    if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
+                }
+            }
+        }
+        __syncthreads();
+        uint32_t *dst = static_cast<uint32_t *>(A.spins);
+        for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = lat[i];
+        return;
+    }
     for (uint32_t i = 0; i < A.nsweeps; ++i) {
         const uint32_t t = A.t0 + i;
         const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
@@ -165,6 +273,74 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny_cluster(const __grid_c
     a.zero = 0u;
     uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;  // t % record_every
     uint32_t slot = 0;
+    if (!FIELD && nwords * S <= nthr) {
+        // Draw-ahead path (see k_tiny): the masks of the next kAheadSweeps
+        // sweeps in one burst, then per step the halos, the bit logic and the
+        // cluster barrier.
+        const bool active = tid < nwords * S;
+        const uint32_t kw = active ? tid / S : 0u, sub = tid % S;
+        const uint32_t ly = kw >> lgW, w = kw & (W - 1u);
+        uint32_t *const row = own + ly * W;  // rows ly - 1 and ly + 1 are in buf as well
+        const uint32_t wl = (w - 1u) & (W - 1u), wr = (w + 1u) & (W - 1u);
+        const uint32_t y = row0 + ly;
+        const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
+        for (uint32_t i0 = 0; i0 < A.nsweeps; i0 += kAheadSweeps) {
+            const uint32_t ns = min(kAheadSweeps, A.nsweeps - i0);
+            uint32_t pk[2 * kAheadSweeps];
+            if (active) tiny_draw_ahead<NQ>(a, A, A.t0 + i0, ns, g, sub * NQ, pk);
+#pragma unroll
+            for (uint32_t j = 0; j < 2 * kAheadSweeps; ++j) {
+                if (j >= 2 * ns) break;
+                const uint32_t p = j & 1u;
+                const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
+                const bool last = i0 + (j >> 1) + 1 == A.nsweeps;
+                const bool count = p == 1u && (rec || last);
+                for (uint32_t h = tid; h < 2 * W; h += nthr) {
+                    if (h < W)
+                        buf[h] = prev[W + (rpc - 1) * W + h];
+                    else
+                        buf[(rpc + 1) * W + (h - W)] = next[W + (h - W)];
+                }
+                __syncthreads();
+                unsigned int cu = 0, ca = 0;
+                if (active) {
+                    const uint32_t nw = update_word32_drawn<NQ>(row[w], row[w - W], row[w + W], row[wl], row[wr],
+                                                                (y + p) & 1u, pk[j], count, cu, ca, sub * NQ);
+                    tiny_store<NQ>(row + w, nw, sub);
+                }
+                if (count) {
+                    cu = __reduce_add_sync(0xFFFFFFFFu, cu);
+                    ca = __reduce_add_sync(0xFFFFFFFFu, ca);
+                    if ((tid & 31u) == 0) {
+                        atomicAdd(&cnt[0], cu);
+                        atomicAdd(&cnt[1], ca);
+                    }
+                }
+                cluster.sync();
+                if (count && tid == 0) {
+                    const unsigned long long c0 = cnt[0], c1 = cnt[1];
+                    if (rec) {
+                        atomicAdd(A.acc + 2 * slot, c0);
+                        atomicAdd(A.acc + 2 * slot + 1, c1);
+                    }
+                    if (last) {
+                        atomicAdd(A.acc + 2 * A.nrec, c0);
+                        atomicAdd(A.acc + 2 * A.nrec + 1, c1);
+                    }
+                    cnt[0] = 0u;
+                    cnt[1] = 0u;
+                }
+                if (p == 1u) {
+                    if (rec) ++slot;
+                    if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
+                }
+            }
+        }
+        uint32_t *dst = static_cast<uint32_t *>(A.spins) + (uint64_t)row0 * W;
+        for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = own[i];
+        cluster.sync();  // no CTA leaves while another may still read its buffer
+        return;
+    }
     for (uint32_t i = 0; i < A.nsweeps; ++i) {
         const uint32_t t = A.t0 + i;
         const bool rec = A.record_every != 0u && phase + 1 == A.record_every;

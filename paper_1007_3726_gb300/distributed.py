@@ -92,8 +92,9 @@ class TorchDistExchange:
 def sweep_strips(strips, exchange, L: int, nsweeps: int, record_every: int = 0):
     """Sweeps the strips (all at the same sweep index) and returns the (M, E)
     samples of the whole lattice at the recorded sweeps."""
+    from . import ising_strip_observables
+
     Ms, Es = [], []
-    N = L * L
     for _ in range(nsweeps):
         t = strips[0].t
         rec = record_every and (t + 1) % record_every == 0
@@ -108,9 +109,9 @@ def sweep_strips(strips, exchange, L: int, nsweeps: int, record_every: int = 0):
             s.t += 1
         if rec:
             c = exchange.sum_counts(strips).cpu()
-            up, anti = int(c[0]), int(c[1])
-            Ms.append(2 * up - N)
-            Es.append(2 * anti - 2 * N)
+            M, E = ising_strip_observables(L, int(c[0]), int(c[1]))
+            Ms.append(M)
+            Es.append(E)
     return Ms, Es
 
 

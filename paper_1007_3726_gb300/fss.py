@@ -6,22 +6,17 @@ cross.
 equilibration samples, and returns U4 with block-bootstrap errors (the samples of
 a Markov chain are correlated: blocks longer than the autocorrelation time are
 resampled).  `crossings` interpolates where the curves of consecutive sizes cross,
-with bootstrap errors.  The moments are computed on the host in FP64 from the
-exact integer samples the GPU records.
+with bootstrap errors.  Each U4 is the library's (ising_measure_from: FP64 sums
+of the exact integer samples in sample order); only the bootstrap replicas,
+which resample blocks of those samples, are formed here.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def binder(M: np.ndarray, N: float) -> float:
-    m = M.astype(np.float64) / N
-    m2 = np.mean(m * m)
-    return float(1.0 - np.mean(m ** 4) / (3.0 * m2 * m2))
-
-
 def bootstrap_binder(M: np.ndarray, N: float, nblocks: int = 50, nboot: int = 200, rng=None):
-    """U4 and its block-bootstrap replicas (nboot values)."""
+    """Block-bootstrap replicas of U4 (nboot values) from the samples M."""
     rng = np.random.default_rng(0) if rng is None else rng
     m = M.astype(np.float64) / N
     n = (len(m) // nblocks) * nblocks
@@ -33,7 +28,7 @@ def bootstrap_binder(M: np.ndarray, N: float, nblocks: int = 50, nboot: int = 20
         k = rng.integers(0, nblocks, size=nblocks)
         s2, s4 = b2[k].mean(), b4[k].mean()
         reps[i] = 1.0 - s4 / (3.0 * s2 * s2)
-    return binder(M[:n], N), reps
+    return reps
 
 
 def run_fss(Ls=(64, 128, 256, 512), temps=None, sweeps=200000, record_every=10, burn_frac=0.2,
@@ -62,7 +57,8 @@ def run_fss(Ls=(64, 128, 256, 512), temps=None, sweeps=200000, record_every=10, 
     for (L, iT), lat in zip(keys, lats):
         burn = int(burn_frac * per_L[L] / record_every)
         M, _ = lat.samples(first=burn)
-        u, reps = bootstrap_binder(M, float(L) * L, rng=rng)
+        u = lat.measure(first_sample=burn)["U4"]
+        reps = bootstrap_binder(M, float(L) * L, rng=rng)
         d = out.setdefault(L, [np.asarray(temps, dtype=np.float64), np.zeros(len(temps)),
                                np.zeros((len(reps), len(temps)))])
         d[1][iT] = u

@@ -164,9 +164,12 @@ def test_fused_counts_equal_recount(P):
 
 def test_large_lattice_L32768(P, orc):
     """L=32768 (2^30 spins, 32-bit words), hot start seed 7, T=2.269185, 1000 sweeps,
-    in the launch configuration the benchmark times.  Checked: the whole initial
-    state, the whole lattice and M/E after sweeps 1 and 2 against the oracle, and
-    at sweep 1000 a 64-row strip (light cone from sweep 996) plus the recount."""
+    in the launch configuration the benchmark times.  Checked against the oracle:
+    the whole initial state; M and E after every one of the first 100 sweeps and
+    the whole lattice at sweep 100 (oracle on the whole lattice, about 75 s of
+    host CPU); and a 2048-row strip at sweep 1000, evolved by the oracle from its
+    own sweep-100 lattice in a light cone (900 sweeps need 1801 rows of margin on
+    each side).  The fused counts of the last sweep equal a GPU recount."""
     L, T, seed = 32768, 2.269185, 7
     thr4, thr8 = orc.thresholds(T)
     lat = P.Lattice(L, T, seed=seed, init="hot", word_bits=32)
@@ -174,18 +177,18 @@ def test_large_lattice_L32768(P, orc):
     assert cfg == lat.launch
     s = orc.init_hot(L, seed)
     assert np.array_equal(lat.spins(), s)
-    M, E = lat.sweep(2, 1, collect=True)
-    Mo, Eo = orc.run(s, 2, seed, 0, thr4, thr8, check=False)
+    M, E = lat.sweep(100, 1, collect=True)
+    Mo, Eo = orc.run(s, 100, seed, 0, thr4, thr8, check=False)
     assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
     assert np.array_equal(lat.spins(), s)
+    row0, rows, k = 20000, 2048, 900
+    margin = 2 * k + 1
+    win = np.ascontiguousarray(s[row0 - margin:row0 + rows + margin])
     del s
-    lat.sweep(994, 1)
-    row0, k, margin = 20000, 4, 2 * 4 + 1
-    win = np.ascontiguousarray(lat.spins(row0 - margin, 64 + 2 * margin))
-    lat.sweep(4, 1)
-    orc.run_window(win, L, row0 - margin, k, seed, 0, thr4, thr8, t0=996)
-    got = lat.spins(row0, 64)
-    assert np.array_equal(win[margin:margin + 64], got)
+    lat.sweep(k, 1)
+    orc.run_window(win, L, row0 - margin, k, seed, 0, thr4, thr8, t0=100)
+    got = lat.spins(row0, rows)
+    assert np.array_equal(win[margin:margin + rows], got)
     d = lat.measure()
     assert d["sweeps_done"] == 1000 and d["n_samples"] == 1000
     assert (d["M"], d["E"]) == lat.recount()

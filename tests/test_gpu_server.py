@@ -84,3 +84,36 @@ def test_poisson_stream_smoke(P):
         out = serve.run_stream(srv, reqs, drain_s=30.0)
     assert out["completed"] == len(reqs) and out["failed"] == 0
     assert out["p50_s"] <= out["p99_s"]
+
+
+def test_served_requests_equal_the_oracle(P, orc):
+    """Six requests of mixed L and T, served together (small epochs, at most three
+    resident, so that they share launches and start at different epochs): every
+    sample and the moments against the oracle run of the same request."""
+    rng = np.random.default_rng(29)
+    reqs = []
+    for i, L in enumerate((64, 128, 256, 512, 128, 320)):
+        reqs.append(dict(L=L, T=float(rng.uniform(1.5, 3.5)), nsweeps=int(rng.integers(40, 120)),
+                         seed=int(rng.integers(0, 2 ** 63)), stream_id=int(rng.integers(0, 2 ** 31)),
+                         record_every=int(rng.choice([1, 4, 5]))))
+    with P.Server(epoch_sweeps=13, max_active=3, keep_samples=True) as srv:
+        ids = [srv.submit(r["L"], r["T"], r["nsweeps"], seed=r["seed"], stream_id=r["stream_id"],
+                          record_every=r["record_every"], tag=i) for i, r in enumerate(reqs)]
+        got = {}
+        while len(got) < len(reqs):
+            for res in srv.poll(wait_s=1.0):
+                got[res["tag"]] = res
+        for i, r in enumerate(reqs):
+            res = got[i]
+            assert res["status"] == P.OK
+            M, E = srv.samples(ids[i])
+            thr4, thr8 = orc.thresholds(r["T"])
+            s = orc.init_hot(r["L"], r["seed"], r["stream_id"])
+            Mo, Eo = orc.run(s, r["nsweeps"], r["seed"], r["stream_id"], thr4, thr8)
+            k = r["record_every"]
+            assert np.array_equal(M, Mo[k - 1::k]) and np.array_equal(E, Eo[k - 1::k]), i
+            obs = res["obs"]
+            assert (obs["M"], obs["E"]) == (Mo[-1], Eo[-1]), i
+            ref = orc.moments(Mo[k - 1::k], Eo[k - 1::k], N=r["L"] ** 2, T=r["T"])
+            for key in ("mean_abs_m", "mean_m2", "mean_m4", "U4", "chi"):
+                assert abs(obs[key] - ref[key]) <= 1e-12 * max(1.0, abs(ref[key])), (i, key)

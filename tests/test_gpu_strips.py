@@ -47,3 +47,25 @@ def test_strip_cold_start_and_errors(P):
         P.ising_strip_step(buf.data_ptr(), 128, 64, 127, 2, 2.0, 1, 0, 0, 0)   # rows beyond L
     with pytest.raises(P.IsingError):
         P.ising_strip_step(buf.data_ptr(), 128, 64, 0, 2, 2.0, 1, 0, 0, 2)     # p out of range
+
+
+@pytest.mark.parametrize("world,L,wb", [(3, 320, 64), (3, 448, 32)])
+def test_three_gpu_strips_equal_the_oracle(P, orc, world, L, wb):
+    """Three strips of uneven height (emulated ranks on one GPU, halo rows copied
+    between them before every step): the whole lattice and every M/E sample
+    against the oracle run of the same lattice."""
+    import torch
+
+    from paper_1007_3726_gb300.distributed import LocalExchange, StripLattice, sweep_strips
+
+    T, seed, sid, n = 2.3, 41, 9, 6
+    strips = [StripLattice(L, T, seed=seed, stream_id=sid, init="hot", rank=k, world=world, word_bits=wb)
+              for k in range(world)]
+    M, E = sweep_strips(strips, LocalExchange(), L, n, 1)
+    thr4, thr8 = orc.thresholds(T)
+    s = orc.init_hot(L, seed, sid)
+    Mo, Eo = orc.run(s, n, seed, sid, thr4, thr8)
+    assert M == [int(v) for v in Mo] and E == [int(v) for v in Eo]
+    packed = torch.cat([st.rows() for st in strips]).cpu().numpy().view(np.uint8).reshape(L, L // 8)
+    spins = np.unpackbits(packed, axis=1, bitorder="little").astype(np.int8) * 2 - 1
+    assert np.array_equal(spins, s)
