@@ -30,6 +30,11 @@ constexpr uint32_t kTinyMaxThreads = 512;
 // single word (the draw-ahead path below): 4 sweeps, 8 checkerboard steps.
 constexpr uint32_t kAheadSweeps = 4;
 
+// Samples the draw-ahead path collects in shared memory before it writes them
+// to global memory in one go: a global write between two steps would make the
+// next barrier (its release side) wait for the write to complete.
+constexpr uint32_t kRingSamples = 64;
+
 // The step-uniform Philox values of sweep t, parity p (as prepare_half_sweep).
 __device__ __forceinline__ void tiny_step_values(HalfSweepArgs &a, const TinyRunArgs &A, uint32_t t, uint32_t p)
 {
@@ -101,10 +106,13 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
     uint32_t slot = 0;
     if (!FIELD && nwords * S <= nthr) {
         // Draw-ahead path: every thread holds at most one word (or its share of
-        // one).  The draws do not depend on the spins, so each thread draws the
-        // masks of its word for the next kAheadSweeps sweeps in one burst (many
-        // independent Philox chains), then every step is the bit logic, a
-        // store and the barrier.
+        // one).  The draws do not depend on the spins, so a thread keeps the
+        // masks of its word for the next 2 kAheadSweeps steps in registers:
+        // after each step's bit logic it draws the masks of the step that many
+        // steps ahead, independent Philox chains that fill the issue slots the
+        // step's dependent logic and the barrier leave idle.
+        __shared__ unsigned int ring[2 * kRingSamples], lastc[2];
+        uint32_t nring = 0;  // samples in the ring; the ring's first is sample `slot`
         const bool active = tid < nwords * S;
         const uint32_t k = active ? tid / S : 0u, sub = tid % S;
         const uint32_t y = k >> lgW, w = k & (W - 1u);
@@ -112,10 +120,10 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
         const uint32_t iu = (y == 0 ? nwords - W : row - W) + w, id = (y + 1 == L ? 0u : row + W) + w;
         const uint32_t il = row + ((w - 1u) & (W - 1u)), ir = row + ((w + 1u) & (W - 1u));
         const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
+        uint32_t pk[2 * kAheadSweeps];
+        if (active) tiny_draw_ahead<NQ>(a, A, A.t0, min(kAheadSweeps, A.nsweeps), g, sub * NQ, pk);
         for (uint32_t i0 = 0; i0 < A.nsweeps; i0 += kAheadSweeps) {
             const uint32_t ns = min(kAheadSweeps, A.nsweeps - i0);
-            uint32_t pk[2 * kAheadSweeps];
-            if (active) tiny_draw_ahead<NQ>(a, A, A.t0 + i0, ns, g, sub * NQ, pk);
 #pragma unroll
             for (uint32_t j = 0; j < 2 * kAheadSweeps; ++j) {
                 if (j >= 2 * ns) break;
@@ -137,27 +145,43 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
                         atomicAdd(&cnt[1], ca);
                     }
                 }
+                // the masks of the same parity kAheadSweeps sweeps later
+                const uint32_t ia = i0 + kAheadSweeps + (j >> 1);
+                if (active && ia < A.nsweeps) {
+                    tiny_step_values(a, A, A.t0 + ia, p);
+                    uint32_t h4[1], h8[1];
+                    word_draw_masks<4, 0, NQ>(a, a, g, h4, h8, sub * NQ);
+                    pk[j] = pack_masks(h4[0], h8[0]);
+                }
                 __syncthreads();
                 if (count && tid == 0) {
-                    const unsigned long long c0 = cnt[0], c1 = cnt[1];
                     if (rec) {
-                        A.acc[2 * slot] = c0;
-                        A.acc[2 * slot + 1] = c1;
+                        ring[2 * nring] = cnt[0];
+                        ring[2 * nring + 1] = cnt[1];
                     }
                     if (last) {
-                        A.acc[2 * A.nrec] = c0;
-                        A.acc[2 * A.nrec + 1] = c1;
+                        lastc[0] = cnt[0];
+                        lastc[1] = cnt[1];
                     }
                     cnt[0] = 0u;
                     cnt[1] = 0u;
                 }
                 if (p == 1u) {
-                    if (rec) ++slot;
+                    if (rec && ++nring == kRingSamples) {
+                        // the ring is full: to global memory (the next counted
+                        // step is two barriers away)
+                        __syncthreads();
+                        for (uint32_t r = tid; r < 2 * kRingSamples; r += nthr) A.acc[2 * slot + r] = ring[r];
+                        slot += kRingSamples;
+                        nring = 0;
+                    }
                     if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
                 }
             }
         }
         __syncthreads();
+        for (uint32_t r = tid; r < 2 * nring; r += nthr) A.acc[2 * slot + r] = ring[r];
+        if (tid < 2) A.acc[2 * A.nrec + tid] = lastc[tid];
         uint32_t *dst = static_cast<uint32_t *>(A.spins);
         for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = lat[i];
         return;
@@ -274,20 +298,28 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny_cluster(const __grid_c
     uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;  // t % record_every
     uint32_t slot = 0;
     if (!FIELD && nwords * S <= nthr) {
-        // Draw-ahead path (see k_tiny): the masks of the next kAheadSweeps
-        // sweeps in one burst, then per step the halos, the bit logic and the
-        // cluster barrier.
+        // Draw-ahead path (see k_tiny).  The cluster barrier is split: a thread
+        // arrives when its step is done, draws the masks of a later step, and
+        // only then waits for the rest of the cluster.  The threads of the
+        // first and last row read the neighbouring CTAs' boundary rows directly
+        // from distributed shared memory: only their bits of the other parity
+        // are used, which the neighbours do not write during this step, and a
+        // neighbour cannot start the next step before this thread has arrived.
+        __shared__ unsigned int ring[2 * kRingSamples], lastc[2];
+        uint32_t nring = 0;  // samples in the ring; the ring's first is sample `slot`
         const bool active = tid < nwords * S;
         const uint32_t kw = active ? tid / S : 0u, sub = tid % S;
         const uint32_t ly = kw >> lgW, w = kw & (W - 1u);
-        uint32_t *const row = own + ly * W;  // rows ly - 1 and ly + 1 are in buf as well
+        uint32_t *const row = own + ly * W;
+        const uint32_t *const upw = ly == 0 ? prev + W + (rpc - 1) * W + w : row + w - W;
+        const uint32_t *const dnw = ly + 1 == rpc ? next + W + w : row + w + W;
         const uint32_t wl = (w - 1u) & (W - 1u), wr = (w + 1u) & (W - 1u);
         const uint32_t y = row0 + ly;
         const uint64_t g = (uint64_t)y * groups_per_row + (uint64_t)w * 4u;
+        uint32_t pk[2 * kAheadSweeps];
+        if (active) tiny_draw_ahead<NQ>(a, A, A.t0, min(kAheadSweeps, A.nsweeps), g, sub * NQ, pk);
         for (uint32_t i0 = 0; i0 < A.nsweeps; i0 += kAheadSweeps) {
             const uint32_t ns = min(kAheadSweeps, A.nsweeps - i0);
-            uint32_t pk[2 * kAheadSweeps];
-            if (active) tiny_draw_ahead<NQ>(a, A, A.t0 + i0, ns, g, sub * NQ, pk);
 #pragma unroll
             for (uint32_t j = 0; j < 2 * kAheadSweeps; ++j) {
                 if (j >= 2 * ns) break;
@@ -295,17 +327,10 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny_cluster(const __grid_c
                 const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
                 const bool last = i0 + (j >> 1) + 1 == A.nsweeps;
                 const bool count = p == 1u && (rec || last);
-                for (uint32_t h = tid; h < 2 * W; h += nthr) {
-                    if (h < W)
-                        buf[h] = prev[W + (rpc - 1) * W + h];
-                    else
-                        buf[(rpc + 1) * W + (h - W)] = next[W + (h - W)];
-                }
-                __syncthreads();
                 unsigned int cu = 0, ca = 0;
                 if (active) {
-                    const uint32_t nw = update_word32_drawn<NQ>(row[w], row[w - W], row[w + W], row[wl], row[wr],
-                                                                (y + p) & 1u, pk[j], count, cu, ca, sub * NQ);
+                    const uint32_t nw = update_word32_drawn<NQ>(row[w], *upw, *dnw, row[wl], row[wr], (y + p) & 1u,
+                                                                pk[j], count, cu, ca, sub * NQ);
                     tiny_store<NQ>(row + w, nw, sub);
                 }
                 if (count) {
@@ -316,26 +341,43 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny_cluster(const __grid_c
                         atomicAdd(&cnt[1], ca);
                     }
                 }
-                cluster.sync();
+                cluster.barrier_arrive();
+                const uint32_t ia = i0 + kAheadSweeps + (j >> 1);
+                if (active && ia < A.nsweeps) {
+                    tiny_step_values(a, A, A.t0 + ia, p);
+                    uint32_t h4[1], h8[1];
+                    word_draw_masks<4, 0, NQ>(a, a, g, h4, h8, sub * NQ);
+                    pk[j] = pack_masks(h4[0], h8[0]);
+                }
+                cluster.barrier_wait();
                 if (count && tid == 0) {
-                    const unsigned long long c0 = cnt[0], c1 = cnt[1];
                     if (rec) {
-                        atomicAdd(A.acc + 2 * slot, c0);
-                        atomicAdd(A.acc + 2 * slot + 1, c1);
+                        ring[2 * nring] = cnt[0];
+                        ring[2 * nring + 1] = cnt[1];
                     }
                     if (last) {
-                        atomicAdd(A.acc + 2 * A.nrec, c0);
-                        atomicAdd(A.acc + 2 * A.nrec + 1, c1);
+                        lastc[0] = cnt[0];
+                        lastc[1] = cnt[1];
                     }
                     cnt[0] = 0u;
                     cnt[1] = 0u;
                 }
                 if (p == 1u) {
-                    if (rec) ++slot;
+                    if (rec && ++nring == kRingSamples) {
+                        // the ring is full: the CTAs add it into the sample slots
+                        __syncthreads();
+                        for (uint32_t r = tid; r < 2 * kRingSamples; r += nthr)
+                            atomicAdd(A.acc + 2 * slot + r, (unsigned long long)ring[r]);
+                        slot += kRingSamples;
+                        nring = 0;
+                    }
                     if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
                 }
             }
         }
+        __syncthreads();
+        for (uint32_t r = tid; r < 2 * nring; r += nthr) atomicAdd(A.acc + 2 * slot + r, (unsigned long long)ring[r]);
+        if (tid < 2) atomicAdd(A.acc + 2 * A.nrec + tid, (unsigned long long)lastc[tid]);
         uint32_t *dst = static_cast<uint32_t *>(A.spins) + (uint64_t)row0 * W;
         for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = own[i];
         cluster.sync();  // no CTA leaves while another may still read its buffer
