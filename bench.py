@@ -225,10 +225,50 @@ def oracle_one_core(target_s: float, rows: int = 64):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def msc_sample(target_s: float):
+    """The paper's CPU multi-spin-coding program (Sec. 4, a Boltzmann-pattern pool
+    of 2^22 entries) on its Table 1 shape, L = 4096 at T = 0.99 T_c, hot start:
+    sweeps until about target_s seconds.  Returns (attempts, seconds, sweeps,
+    threads)."""
+    from oracle import msc
+
+    import oracle
+
+    L4 = 4096
+    pool = msc.Pool(0.99 * 2.269185, 1 << 22, seed=1)
+    lat = msc.pack(oracle.init_hot(L4, 11, 0))
+    msc.sweeps(lat, pool, 1, seed=1, record=False)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        msc.sweeps(lat, pool, 1, seed=1, t0=1 + n, record=False)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return L4 * L4 * n, el, n, threads
+
+
+def msc_one_core(target_s: float):
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = "import json, bench; print(json.dumps(bench.msc_sample(%r)))" % target_s
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def cpu_baseline(target_s=10.0):
     a, el, sw, thr = oracle_window_sample(target_s)
     a1, el1, sw1, thr1 = oracle_one_core(target_s)
-    return {"value": a / el / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
+    m, elm, swm, thrm = msc_sample(5.0)
+    m1, elm1, swm1, thrm1 = msc_one_core(5.0)
+    msc = {"kind": "the paper's CPU multi-spin coding (Sec. 4), Boltzmann-pattern pool of 2^22, one address "
+                   "per 32-spin word; not bit-exact (another random-number scheme), pinned statistically",
+           "workload": "L=4096, T=0.99 T_c, hot start (the paper's Table 1 shape)", "unit": UNIT,
+           "all_cores": {"value": m / elm / 1e9, "cores": thrm, "sweeps": swm, "seconds": elm},
+           "one_core": {"value": m1 / elm1 / 1e9, "cores": thrm1, "sweeps": swm1, "seconds": elm1},
+           "paper_one_core": {"value": 0.2267, "hardware": "Intel Xeon X5560 2.80 GHz, 1 core (Table 1)"}}
+    return {"value": a / el / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle", "paper_cpu_msc": msc,
             "sample": "oracle (one int8 per spin, plain C, OpenMP over rows) on rows 0-255 of the "
                       "L=524288 cold start, %d sweeps in light-cone mode, %.1f s wall, %d threads"
                       % (sw, el, thr),

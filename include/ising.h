@@ -193,6 +193,11 @@ ISING_API ising_status ising_recount(ising_lattice *h, int64_t *M, int64_t *E);
 ISING_API ising_status ising_info(const ising_lattice *h, uint32_t *word_bits, uint64_t *L,
                         uint64_t *sweeps_done);
 
+/* Memory check (a stand-in for a device memory checker): every lattice
+ * allocation carries 256 guard bytes of 0xA5 before and after the lattice.
+ * Sets *intact to 1 while both guards are unchanged, 0 if any kernel wrote
+ * past the lattice.  Waits for the handle's stream. */
+ISING_API ising_status ising_check_guards(ising_lattice *h, uint32_t *intact);
 /* Device address of the packed lattice and its size in bytes (owned by the handle). */
 ISING_API ising_status ising_device_spins(const ising_lattice *h, void **dptr, size_t *bytes);
 

@@ -56,7 +56,8 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    # ISING_ORACLE_LIB: another build of ising_oracle.c (the sanitizer tests)
+    lib = ctypes.CDLL(os.environ.get("ISING_ORACLE_LIB") or build())
     lib.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
     lib.orc_philox_batch.argtypes = [ctypes.c_uint64, _u32p, _u32p, _u32p]
     lib.orc_thresholds.argtypes = [ctypes.c_double, _u32p, _u32p]

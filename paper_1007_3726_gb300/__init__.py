@@ -22,7 +22,7 @@ __all__ = [
     "IsingError", "Lattice", "build", "load", "thresholds", "ising_create", "ising_sweep",
     "ising_measure", "ising_measure_from", "ising_destroy", "ising_get_spins", "ising_get_packed", "ising_recount", "ising_get_samples",
     "ising_thresholds", "ising_last_error", "ising_set_allocator", "ising_info",
-    "ising_device_spins", "ising_sweep_noalloc", "ising_bench_mix", "ising_strip_init", "ising_strip_step", "ising_strip_observables", "ising_get_launch", "ising_set_launch",
+    "ising_device_spins", "ising_check_guards", "ising_sweep_noalloc", "ising_bench_mix", "ising_strip_init", "ising_strip_step", "ising_strip_observables", "ising_get_launch", "ising_set_launch",
     "ising_launch_candidates", "ising_autotune", "ising_sweep_batch", "ising_batch_tune", "Batch", "Server", "IsingBatchOpts",
     "IsingParams", "IsingLaunch", "IsingObs", "INIT_MODES", "STATUS_NAMES",
 ]
@@ -178,6 +178,7 @@ def load(path: str | None = None):
         "ising_set_field": ([H, ctypes.c_double], ctypes.c_int),
         "ising_get_params": ([H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                              ctypes.c_int),
+        "ising_check_guards": ([H, _u32p], ctypes.c_int),
         "ising_strip_observables": ([ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _i64p, _i64p],
                                     ctypes.c_int),
         "ising_bench_mix": ([ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
@@ -503,6 +504,17 @@ def ising_strip_step(d_rows: int, L: int, word_bits: int, row0: int, nrows: int,
                                    d_counts, _stream_ptr(stream)))
 
 
+def ising_check_guards(h) -> bool:
+    """True while the guard bytes around the handle's lattice are intact."""
+    v = ctypes.c_uint32()
+    _check(load().ising_check_guards(h, ctypes.byref(v)))
+    return bool(v.value)
+
+
+# guard failures seen when lattices were closed (checked after every GPU test)
+guard_failures: list = []
+
+
 def ising_strip_observables(L: int, n_up: int, n_anti: int) -> tuple[int, int]:
     """(M, E) of an L x L lattice from its summed step-B counts (see include/ising.h)."""
     M = ctypes.c_int64()
@@ -664,9 +676,17 @@ class Lattice:
     def sweeps_done(self) -> int:
         return ising_info(self._h)[2]
 
+    def guards_intact(self) -> bool:
+        return ising_check_guards(self._h)
+
     def close(self):
         if self._h is not None:
             h, self._h = self._h, None
+            try:
+                if not ising_check_guards(h):
+                    guard_failures.append((self.L, self.seed, self.stream_id))
+            except IsingError:
+                pass  # a failed handle: its error was reported where it happened
             ising_destroy(h)
 
     def __del__(self):

@@ -1059,6 +1059,7 @@ ISING_API ising_status ising_batch_create(ising_lattice *const *hs, uint32_t n, 
 
 ISING_API ising_status ising_batch_run(ising_batch *b, uint32_t runs)
 {
+    NvtxRange range("ising_batch_run");
     clear_error();
     if (!b) return fail(ISING_ERR_INVALID, "null batch");
     if (b->failed) return fail(ISING_ERR_STATE, "batch failed earlier");

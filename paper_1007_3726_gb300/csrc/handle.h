@@ -23,7 +23,8 @@ struct ising_lattice {
     int device = 0;
     cudaStream_t stream = nullptr;
     ising::Allocator alloc;
-    void *d_spins = nullptr;
+    void *d_base = nullptr;   // the allocation: guard, lattice, guard
+    void *d_spins = nullptr;  // the lattice, kGuardBytes into d_base
     unsigned long long *d_acc = nullptr;  // 2 counters per slot
     unsigned long long *h_acc = nullptr;  // pinned mirror
     size_t acc_slots = 0;
@@ -41,6 +42,11 @@ struct ising_lattice {
 
 
 namespace ising {
+// Guard bytes before and after every lattice allocation, filled with
+// kGuardByte; ising_check_guards tells whether they are still intact.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
 // Launch configuration for a new handle: the autotuned one for (device, L,
 // word width) if there is one, else a fixed default.
 LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits);

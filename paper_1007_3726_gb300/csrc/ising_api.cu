@@ -164,7 +164,7 @@ void destroy_all(ising_lattice *h)
     if (!h) return;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
-    h->alloc.release(h->d_spins, h->stream);
+    h->alloc.release(h->d_base, h->stream);
     h->alloc.release(h->d_acc, h->stream);
     if (h->h_acc) cudaFreeHost(h->h_acc);
     if (h->ev) cudaEventDestroy(h->ev);
@@ -319,9 +319,14 @@ ising_status ising_create(const ising_params *params, void *cuda_stream, ising_l
         h->ev = nullptr;
         return bail(fail(ISING_ERR_CUDA, "cudaEventCreate failed"));
     }
-    h->d_spins = h->alloc.allocate(h->bytes, h->stream);
-    if (!h->d_spins)
+    h->d_base = h->alloc.allocate(h->bytes + 2 * kGuardBytes, h->stream);
+    if (!h->d_base)
         return bail(fail(ISING_ERR_OOM, "cannot allocate %zu bytes for the lattice", h->bytes));
+    h->d_spins = static_cast<char *>(h->d_base) + kGuardBytes;
+    e = cudaMemsetAsync(h->d_base, kGuardByte, kGuardBytes, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(static_cast<char *>(h->d_spins) + h->bytes, kGuardByte, kGuardBytes, h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "guard bytes"));
     if ((st = ensure_acc(h, 64)) != ISING_OK) return bail(st);
 
     h->launch = default_launch(h->device, h->L, wb);
@@ -382,6 +387,7 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
                          int64_t *E_out, uint64_t cap)
 {
     clear_error();
+    NvtxRange range("ising_sweep");
     ising_status st = check_live(h);
     if (st != ISING_OK) return st;
     if ((M_out == nullptr) != (E_out == nullptr))
@@ -627,6 +633,23 @@ ising_status ising_info(const ising_lattice *h, uint32_t *word_bits, uint64_t *L
     if (word_bits) *word_bits = h->word_bits;
     if (L) *L = h->L;
     if (sweeps_done) *sweeps_done = h->sweeps_done;
+    return ISING_OK;
+}
+
+ising_status ising_check_guards(ising_lattice *h, uint32_t *intact)
+{
+    clear_error();
+    ising_status st = check_live(h);
+    if (st != ISING_OK) return st;
+    if (!intact) return fail(ISING_ERR_INVALID, "intact is NULL");
+    unsigned char g[2 * kGuardBytes];
+    CK(h, cudaMemcpyAsync(g, h->d_base, kGuardBytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(g + kGuardBytes, static_cast<char *>(h->d_spins) + h->bytes, kGuardBytes,
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    uint32_t ok = 1;
+    for (size_t i = 0; i < 2 * kGuardBytes; ++i) ok &= (g[i] == kGuardByte);
+    *intact = ok;
     return ISING_OK;
 }
 

@@ -7,8 +7,18 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace ising {
+
+// An NVTX range for the lifetime of the object (visible in Nsight timelines;
+// without a tool attached a push / pop costs a few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Sets the calling thread's last-error text and returns st.
 ising_status fail(ising_status st, const char *fmt, ...);

@@ -104,6 +104,7 @@ void finish(ising_server *s, Request *r, ising_status st)
 // Admits queued requests, in arrival order, while the budget allows.
 void admit(ising_server *s)
 {
+    NvtxRange range("server_admit");
     while (true) {
         Request *r = nullptr;
         {
@@ -142,6 +143,7 @@ void admit(ising_server *s)
 // One launch over the oldest resident requests that fit the batch.
 void run_epoch(ising_server *s)
 {
+    NvtxRange range("server_epoch");
     std::vector<Request *> res;
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -160,3 +160,73 @@ class StripLattice:
     def rows(self):
         """The strip's packed rows (without halos)."""
         return self.buf[1:self.nrows + 1]
+
+
+# ---------------------------------------------------- independent lattices --
+def lpt_partition(work, world: int) -> list[list[int]]:
+    """Longest-processing-time split of independent jobs over `world` ranks: the
+    jobs in order of decreasing work (ties by index), each to the rank with the
+    least work so far (ties to the lowest rank).  Returns each rank's job
+    indices in increasing order.  Deterministic, so every rank computes the same
+    split without communicating."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0] * world
+    parts: list[list[int]] = [[] for _ in range(world)]
+    for i in sorted(range(len(work)), key=lambda k: (-work[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += work[i]
+    return [sorted(p) for p in parts]
+
+
+def run_sharded(specs, runner, group=None):
+    """Runs independent lattices (or requests) spread over the ranks of a
+    torch.distributed group by lpt_partition of their work L^2 x sweeps:
+    runner(list of specs) runs one rank's share and returns one result per
+    spec; the results of all ranks are gathered on every rank and returned in
+    the order of `specs`.  A lattice's results depend only on its own seed,
+    stream and sweeps, so they equal a one-rank run of the same specs.  With
+    no initialised process group the call runs everything on this process."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return list(runner(list(specs)))
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    parts = lpt_partition([int(s["L"]) ** 2 * int(s["sweeps"]) for s in specs], world)
+    mine = parts[rank]
+    res = list(runner([specs[i] for i in mine]))
+    if len(res) != len(mine):
+        raise RuntimeError("runner returned %d results for %d specs" % (len(res), len(mine)))
+    gathered = [None] * world
+    dist.all_gather_object(gathered, list(zip(mine, res)), group=group)
+    out = [None] * len(specs)
+    for chunk in gathered:
+        for i, r in chunk:
+            out[i] = r
+    return out
+
+
+def batch_runner(record_every: int, batch_opts=None):
+    """A runner for run_sharded on this rank's GPU: the specs' lattices in one
+    persistent batch launch; each result is the lattice's samples (M, E) and
+    its FP64 moments."""
+
+    def run(specs):
+        from . import Batch, Lattice
+
+        if not specs:
+            return []
+        keys = ("L", "T", "seed", "stream_id", "init", "word_bits")
+        lats = [Lattice(**{k: sp[k] for k in keys if k in sp}) for sp in specs]
+        with Batch(lats, [sp["sweeps"] for sp in specs], record_every, **(batch_opts or {})) as b:
+            b.run(1)
+        out = []
+        for lat in lats:
+            M, E = lat.samples()
+            out.append({"M": M, "E": E, "obs": lat.measure()})
+            lat.close()
+        return out
+
+    return run

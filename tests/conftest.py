@@ -19,3 +19,20 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(autouse=True)
+def _lattice_guards_intact(request):
+    """After every GPU test: no lattice closed during it had a guard byte
+    (around its device allocation) overwritten."""
+    yield
+    if request.node.get_closest_marker("gpu") is None:
+        return
+    import gc
+
+    import paper_1007_3726_gb300 as P
+
+    gc.collect()  # close the lattices the test left to the garbage collector
+    bad = list(P.guard_failures)
+    P.guard_failures.clear()
+    assert not bad, "guard bytes overwritten around lattices %r" % bad

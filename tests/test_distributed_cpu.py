@@ -95,3 +95,62 @@ def test_strips_over_gloo_ranks_equal_whole_lattice(orc, world, L):
     Mo, Eo = orc.run(s, n, 9, 2, thr4, thr8)
     assert np.array_equal(full, s)
     assert M == [int(v) for v in Mo[rec - 1::rec]] and E == [int(v) for v in Eo[rec - 1::rec]]
+
+
+def test_lpt_partition_balances_and_covers():
+    from paper_1007_3726_gb300.distributed import lpt_partition
+
+    work = [256 ** 2 * 10000] * 32 + [512 ** 2 * 10000] * 32 + [1024 ** 2 * 10000] * 32 + \
+           [2048 ** 2 * 10000] * 32
+    for world in (1, 2, 3, 4, 8):
+        parts = lpt_partition(work, world)
+        assert sorted(i for p in parts for i in p) == list(range(len(work)))
+        loads = [sum(work[i] for i in p) for p in parts]
+        # LPT: the heaviest rank exceeds the mean by at most the largest job
+        assert max(loads) - sum(work) / world <= max(work)
+    # 5 -> rank 0, 4 -> rank 1, 2 -> rank 1 (4 < 5), 1 -> rank 0 (5 < 6)
+    assert lpt_partition([5, 1, 4, 2], 2) == [[0, 1], [2, 3]]
+    with pytest.raises(ValueError):
+        lpt_partition([1], 0)
+
+
+def _oracle_runner(specs):
+    import oracle
+
+    out = []
+    for sp in specs:
+        thr4, thr8 = oracle.thresholds(sp["T"])
+        s = oracle.init_hot(sp["L"], sp["seed"], sp["stream_id"])
+        M, E = oracle.run(s, sp["sweeps"], sp["seed"], sp["stream_id"], thr4, thr8)
+        out.append((M.tolist(), E.tolist(), s.tobytes()))
+    return out
+
+
+def _sharded_worker(rank, world, port, specs, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1007_3726_gb300.distributed import run_sharded
+
+        res = run_sharded(specs, _oracle_runner)
+        if rank == 0:
+            q.put(res)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_lattices_over_gloo_ranks_equal_one_rank(orc, world):
+    """Independent lattices of uneven size split over gloo ranks by LPT: every
+    lattice's samples and final state equal the one-rank run."""
+    rng = np.random.default_rng(5)
+    specs = [dict(L=int(L), T=float(rng.uniform(1.8, 3.0)), seed=3, stream_id=i, sweeps=int(rng.integers(3, 9)))
+             for i, L in enumerate([8, 16, 24, 8, 32, 12, 16, 40, 8])]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    mp.start_processes(_sharded_worker, args=(world, port, specs, q), nprocs=world, join=True,
+                       start_method="spawn")
+    got = q.get(timeout=60)
+    assert got == _oracle_runner(specs)
