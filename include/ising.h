@@ -235,9 +235,16 @@ ISING_API const char *ising_last_error(void);
  * grid the CTAs: 1, or a thread-block cluster of 2, 4 or 8 CTAs that split
  * the rows and read their neighbours' boundary rows from distributed shared
  * memory, with a cluster barrier between the steps; regcap = insert = 0.  It is
- * the default for L <= 512 (one CTA at L = 64, a cluster of 8 above).  In a
- * field (H != 0) it uses one thread per word whatever rows_per_item says; the
- * step kernels are then replaced by the field step kernel.
+ * the default for L <= 512 (one CTA at L = 64, a cluster of 8 above).  At
+ * L = 64 the one-CTA configuration with block 512 and one thread per word is
+ * warp-specialised: four warps update the words, twelve draw the acceptance
+ * masks of later steps into a ring in shared memory, handed over through
+ * mbarriers whose waits are bounded (when one runs out the call returns
+ * ISING_ERR_TIMEOUT and the handle is failed; the environment variable
+ * ISING_TINY_HOLD_STEP = 1 + a step index withholds that step's masks, for
+ * failure-detection tests only).  In a field (H != 0) it uses one thread per
+ * word whatever rows_per_item says; the step kernels are then replaced by the
+ * field step kernel.
  * persistent = 1 (with proc_bits 32 or 64, insert 0, grid 0; regcap 0, 1 or
  * 2 = the compiler's choice, <= 40 or <= 64 registers)
  * runs every sweep of an ising_sweep call in one cooperative launch of that
@@ -465,7 +472,7 @@ ISING_API ising_status ising_strip_observables(uint64_t L, uint64_t n_up, uint64
  * call returns once the work is queued.
  *
  * Scratch: the per-sweep counters live in a fixed device array compiled into
- * the library, ISING_NOALLOC_MAX_RECORDS samples plus one slot (1 MiB) that every GPU which
+ * the library, ISING_NOALLOC_MAX_RECORDS samples plus two slots (1 MiB) that every GPU which
  * loads the library holds until the process exits.  A call that would record
  * more samples fails with ISING_ERR_INVALID before any work; split it.  All
  * calls share that array and it keeps the previous call's contents (the call

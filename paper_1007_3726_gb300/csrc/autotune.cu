@@ -44,7 +44,7 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
     // untuned: the shapes the autotuner picked on GB300 at these sizes
     // (fields: proc_bits, regcap, insert, block, rows_per_item, grid)
     // one CTA (L = 64) or a cluster of 8 CTAs (L = 128 .. 512): every sweep of a call in one launch
-    if (L == 64) return LaunchConfig{kTinyProcBits, 0, 0, 256, 2, 1};
+    if (L == 64) return LaunchConfig{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 1};  // warp-specialised
     if (L == 128) return LaunchConfig{kTinyProcBits, 0, 0, 128, 2, 8};
     if (L == 256) return LaunchConfig{kTinyProcBits, 0, 0, 256, 1, 8};
     if (L == 512) return LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 8};
@@ -62,7 +62,12 @@ void remember_launch(int device, uint64_t L, uint32_t word_bits, const LaunchCon
 std::vector<LaunchConfig> launch_candidates(uint64_t L, uint64_t rows)
 {
     std::vector<LaunchConfig> out;
-    // the one-CTA kernel, for lattices one CTA holds
+    // the one-CTA kernel, for lattices one CTA holds (and its warp-specialised
+    // form at L = 64)
+    {
+        LaunchConfig ws{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 1};
+        if (launch_config_valid(ws, L, rows)) out.push_back(ws);
+    }
     for (uint32_t ctas : {1u, 2u, 4u, 8u})
         for (uint32_t blk : {128u, 256u, 512u})
             for (uint32_t tpw : {1u, 2u, 4u}) {
@@ -205,8 +210,10 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
             ta.record_every = 0;
             ta.nrec = 0;
             ta.acc = h->d_acc;
+            ta.err = reinterpret_cast<unsigned int *>(h->d_acc + 2);  // after the one state slot
             ta.nsweeps = 1;
-            e = launch_tiny(ta, c.block, c.rows_per_item, c.grid, h->stream);
+            e = cudaMemsetAsync(h->d_acc + 2, 0, 16, h->stream);
+            if (e == cudaSuccess) e = launch_tiny(ta, c.block, c.rows_per_item, c.grid, h->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
             ta.nsweeps = 8 * reps;
             if (e == cudaSuccess) e = launch_tiny(ta, c.block, c.rows_per_item, c.grid, h->stream);
@@ -223,6 +230,17 @@ ISING_API ising_status ising_autotune(ising_lattice *h, uint32_t reps, ising_lau
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess && c.proc_bits == kTinyProcBits) {
+            unsigned int flag = 0;
+            e = cudaMemcpy(&flag, h->d_acc + 2, sizeof flag, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && flag) {
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
+                h->alloc.release(scratch, h->stream);
+                h->failed = true;
+                return fail(ISING_ERR_TIMEOUT, "a wait inside the one-CTA kernel ran out during autotuning");
+            }
+        }
         float ms = 0;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         const double step_ms = (double)ms / steps;

@@ -37,6 +37,7 @@ struct ising_lattice {
     // samples of the last queued call, read back at the next synchronising call
     bool pending = false;
     size_t pending_rec = 0;  // recorded slots of that call
+    bool pending_err = false;  // slot pending_rec + 1 holds a kernel's error flag
     bool failed = false;
 };
 

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -125,6 +126,14 @@ ising_status harvest(ising_lattice *h)
 {
     if (!h->pending) return ISING_OK;
     CK(h, cudaEventSynchronize(h->ev));
+    if (h->pending_err && h->h_acc[2 * (h->pending_rec + 1)] != 0) {
+        // a bounded wait in the kernel ran out: the lattice is not to be trusted
+        h->pending = false;
+        h->pending_err = false;
+        h->failed = true;
+        return fail(ISING_ERR_TIMEOUT, "a wait inside the one-CTA kernel ran out; the lattice is lost");
+    }
+    h->pending_err = false;
     for (size_t i = 0; i < h->pending_rec; ++i) {
         h->sM.push_back(to_M(h, h->h_acc[2 * i]));
         h->sE.push_back(to_E(h, h->h_acc[2 * i + 1]));
@@ -404,9 +413,9 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
         return fail(ISING_ERR_INVALID, "cap %llu < %llu samples of this call",
                     (unsigned long long)cap, (unsigned long long)nrec);
     if ((st = harvest(h)) != ISING_OK) return st;
-    if ((st = ensure_acc(h, nrec + 1)) != ISING_OK) return st;
+    if ((st = ensure_acc(h, nrec + 2)) != ISING_OK) return st;
 
-    CK(h, cudaMemsetAsync(h->d_acc, 0, (nrec + 1) * 16, h->stream));
+    CK(h, cudaMemsetAsync(h->d_acc, 0, (nrec + 2) * 16, h->stream));
     if (h->launch.proc_bits == kTinyProcBits) {
         // the whole call in one launch of one CTA
         TinyRunArgs ta{};
@@ -427,7 +436,14 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
             ta.k_up = h->field.k_up;
             ta.k_dn = h->field.k_dn;
         }
+        ta.err = reinterpret_cast<unsigned int *>(h->d_acc + 2 * (nrec + 1));
+        {
+            // failure-detection testing only (see include/ising.h)
+            const char *hold = std::getenv("ISING_TINY_HOLD_STEP");
+            ta.hold_step = hold ? (uint32_t)std::strtoul(hold, nullptr, 10) : 0u;
+        }
         CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->launch.grid, h->stream));
+        h->pending_err = true;
         return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
     }
     if (h->launch.persistent && h->H == 0.0) {
@@ -494,7 +510,8 @@ ising_status finish_sweep_call(ising_lattice *h, uint64_t t0, uint64_t nsweeps, 
                                int64_t *E_out)
 {
     ising_status st;
-    CK(h, cudaMemcpyAsync(h->h_acc, h->d_acc, (nrec + 1) * 16, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_acc, h->d_acc, (nrec + (h->pending_err ? 2 : 1)) * 16, cudaMemcpyDeviceToHost,
+                          h->stream));
     CK(h, cudaEventRecord(h->ev, h->stream));
     h->sweeps_done = t0 + nsweeps;
     h->pending = true;

@@ -121,7 +121,17 @@ struct TinyRunArgs {
     uint32_t use_field;
     uint32_t field_thr[16];
     uint32_t k_up, k_dn;
+    // set to a nonzero value by a kernel whose bounded wait ran out (the
+    // warp-specialised one-CTA kernel); must be zero at the launch, may be null
+    unsigned int *err;
+    // failure-detection testing only: 1 + a step whose masks the producers of
+    // the warp-specialised kernel never announce (0 = none), so that the
+    // consumers' wait runs out (with a short wait limit)
+    uint32_t hold_step;
 };
+// The warp-specialised one-CTA configuration: L = 64, 1024 threads, one thread
+// per word (tiny.cu): four warps update the words, 28 draw the masks.
+constexpr uint32_t kTinyWsL = 64, kTinyWsBlock = 1024;
 // ctas = 1: one CTA; 2, 4, 8: a cluster of CTAs, each with L / ctas rows.
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, uint32_t ctas,
                         cudaStream_t s);

@@ -25,10 +25,11 @@ namespace {
 
 // Two 64-bit counters per recorded sweep (number of +1 spins, number of
 // anti-aligned bonds), plus one slot for the state after the call's last sweep
-// that the one-CTA and cluster kernels always write.  Every GPU that loads the
-// library holds this 1 MiB (and 16 bytes) until the process exits.
+// that the one-CTA and cluster kernels always write and one for their error
+// flag.  Every GPU that loads the library holds this 1 MiB (and 32 bytes)
+// until the process exits.
 constexpr uint64_t kMaxRecords = ISING_NOALLOC_MAX_RECORDS;
-static __device__ __align__(256) unsigned long long g_noalloc_counters[2 * (kMaxRecords + 1)];
+static __device__ __align__(256) unsigned long long g_noalloc_counters[2 * (kMaxRecords + 2)];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -137,8 +138,10 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
         ta.record_every = record_every;
         ta.nrec = (uint32_t)nrec;
         ta.acc = acc;
-        // the cluster kernel adds into every slot it writes, the last one included
-        e = cudaMemsetAsync(acc, 0, (nrec + 1) * 2 * sizeof(unsigned long long), s);
+        // the cluster kernel adds into every slot it writes, the last one included;
+        // the slot after it is the error flag of the one-CTA kernels
+        ta.err = reinterpret_cast<unsigned int *>(acc + 2 * (nrec + 1));
+        e = cudaMemsetAsync(acc, 0, (nrec + 2) * 2 * sizeof(unsigned long long), s);
         if (e == cudaSuccess) e = launch_tiny(ta, dflt.block, dflt.rows_per_item, dflt.grid, s);
     }
     const LaunchConfig cfg = plain_launch(dflt);
@@ -154,6 +157,9 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
             e = launch_half_sweep(a, cfg, s);
         }
     }
+    unsigned long long err_flag = 0;
+    if (e == cudaSuccess && nrec && dflt.proc_bits == kTinyProcBits)
+        e = cudaMemcpyAsync(&err_flag, acc + 2 * (nrec + 1), sizeof err_flag, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && nrec) {
         // column 0 of the counters into M_out, column 1 into E_out
         e = cudaMemcpy2DAsync(M_out, sizeof(int64_t), acc, 2 * sizeof(unsigned long long),
@@ -164,6 +170,7 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
     }
     if (e == cudaSuccess && nrec) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(ISING_ERR_CUDA, "ising_sweep_noalloc: %s", cudaGetErrorString(e));
+    if (err_flag) return fail(ISING_ERR_TIMEOUT, "a wait inside the one-CTA kernel ran out; the lattice is lost");
     const int64_t N = (int64_t)(L * L);
     for (uint64_t i = 0; i < nrec; ++i) {
         M_out[i] = 2 * M_out[i] - N;      // +1 spins -> magnetisation

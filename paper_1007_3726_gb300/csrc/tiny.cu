@@ -254,6 +254,189 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
     for (uint32_t i = tid; i < nwords; i += nthr) dst[i] = lat[i];
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised one-CTA kernel for L = 64 (128 words of 32 bits).  With one
+// SM for the whole lattice a step is short, and when every thread both draws
+// and updates, the dependent bit logic and the barrier of each step leave most
+// issue slots idle.  Here the roles are split:
+//   warps 0-3   consumers: thread c updates word c at every step (the bit logic
+//               with the masks read from shared memory, the store, the counts);
+//   warps 4-31  producers: seven groups of 128 threads; group g draws the masks
+//               of steps g, g + 7, g + 14, ... for word (thread index mod 128)
+//               into a ring of kWsSlots steps in shared memory (seven steps in
+//               flight give the Philox chains enough warps to hide their
+//               latency).
+// The masks do not depend on the spins, so the producers run ahead of the
+// consumers by up to kWsSlots steps.  A ring entry is one 64-bit word, the
+// masks and the tag s + 1 of their step, written with one store: the consumer
+// of word c spins on its entry until the tag is there (a shared-memory load,
+// short latency).  Having read it, the consumer arrives on the slot's "empty"
+// mbarrier; the producers wait on that mbarrier before they reuse the slot
+// (a suspended wait, so that waiting producers leave the issue slots to the
+// consumers).  A named barrier of the consumers ends each step.  Every wait is
+// bounded: when one runs out, the kernel sets `abort` (the consumers all stop
+// after the same barrier, the producers leave) and *err, so the kernel always
+// ends.
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    // the state token goes to the sink: no register waits for the arrival
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Waits (bounded: at most `limit` polls, each of which may suspend the thread
+// for a while without using issue slots) until the phase of the given parity
+// has completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+constexpr uint32_t kWsSlots = 8;
+constexpr uint32_t kWsWords = 128;
+constexpr uint32_t kWsGroups = kTinyWsBlock / kWsWords - 1;  // producer groups (7)
+constexpr uint32_t kWsSpinLimit = 1u << 24;  // polls of a consumer's wait before it gives up
+constexpr uint32_t kWsWaitLimit = 1u << 20;  // polls of a producer's mbarrier wait
+
+__global__ void __launch_bounds__(kTinyWsBlock) k_tiny_ws(const __grid_constant__ TinyRunArgs A)
+{
+    __shared__ uint32_t lat[kWsWords];
+    __shared__ uint64_t entries[kWsSlots][kWsWords];  // (step + 1) << 32 | masks
+    __shared__ __align__(8) uint64_t empty[kWsSlots];  // 128 consumer arrivals: the slot is read
+    // per consumer warp (+1 spins, anti-aligned bonds) of up to kRingSamples
+    // samples, and of the state after the last sweep
+    __shared__ unsigned int wring[kRingSamples + 1][4][2], ws_abort;
+    volatile uint64_t *const ve = &entries[0][0];
+    volatile unsigned int *const vabort = &ws_abort;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t L = kTinyWsL, W = 2, nsteps = 2 * A.nsweeps;
+    const uint64_t groups_per_row = L >> 3;
+    // a held step (failure testing) runs the waits out quickly
+    const uint32_t limit = A.hold_step ? (1u << 14) : kWsSpinLimit;
+    const uint32_t plimit = A.hold_step ? (1u << 12) : kWsWaitLimit;
+    const uint32_t *src = static_cast<const uint32_t *>(A.spins);
+    if (tid < kWsWords) {
+        lat[tid] = src[tid];
+        for (uint32_t k = 0; k < kWsSlots; ++k) entries[k][tid] = 0ull;
+    }
+    if (tid == 0) {
+        ws_abort = 0u;
+        for (uint32_t k = 0; k < kWsSlots; ++k) mbar_init(&empty[k], kWsWords);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();  // the last barrier of the whole block
+
+    HalfSweepArgs a;
+    a.key = A.key;
+    a.thr4 = A.thr4;
+    a.thr8 = A.thr8;
+    a.zero = 0u;
+    if (tid >= kWsWords) {
+        // ---- producers
+        const uint32_t pt = tid - kWsWords, grp = pt / kWsWords, w = pt % kWsWords;
+        const uint64_t g = (uint64_t)(w >> 1) * groups_per_row + (uint64_t)(w & 1u) * 4u;
+        for (uint32_t s = grp; s < nsteps; s += kWsGroups) {
+            const uint32_t k = s % kWsSlots;
+            if (s >= kWsSlots && !mbar_wait(&empty[k], ((s / kWsSlots) & 1u) ^ 1u, plimit)) {
+                // the consumers did not read the slot's previous entry in time
+                *vabort = 1u;
+                if (A.err) atomicExch(A.err, 1u);
+                return;
+            }
+            tiny_step_values(a, A, A.t0 + (s >> 1), s & 1u);
+            uint32_t h4[1], h8[1];
+            word_draw_masks<4, 0, 4>(a, a, g, h4, h8);
+            if (A.hold_step == s + 1) continue;  // never published (failure testing)
+            ve[k * kWsWords + w] = ((uint64_t)(s + 1) << 32) | pack_masks(h4[0], h8[0]);
+        }
+        return;
+    }
+    // ---- consumers: thread c updates word c (row c / 2, word c % 2).  A step
+    // ends with a named barrier of the 128 consumers (bar.sync 1, 128); no
+    // consumer leaves the loop alone, so every barrier completes.
+    const uint32_t c = tid, y = c >> 1, w = c & 1u;
+    const uint32_t row = c - w;
+    const uint32_t iu = (y == 0 ? kWsWords - W : row - W) + w, id = (y + 1 == L ? 0u : row + W) + w;
+    const uint32_t inb = row + (w ^ 1u);  // W = 2: the left and the right neighbour word
+    uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;
+    uint32_t slot = 0, nring = 0;
+    for (uint32_t s = 0; s < nsteps; ++s) {
+        const uint32_t k = s % kWsSlots, p = s & 1u;
+        const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
+        const bool last = (s >> 1) + 1 == A.nsweeps;
+        const bool count = p == 1u && (rec || last);
+        unsigned int cu = 0, ca = 0;
+        uint64_t e = ve[k * kWsWords + c];
+        uint32_t i = 0;
+        while ((uint32_t)(e >> 32) != s + 1 && ++i < limit) e = ve[k * kWsWords + c];
+        if ((uint32_t)(e >> 32) == s + 1) {
+            mbar_arrive(&empty[k]);  // this thread has read the slot (release: after the load)
+            const uint32_t nw = update_word32_drawn<4>(lat[c], lat[iu], lat[id], lat[inb], lat[inb], (y + p) & 1u,
+                                                       (uint32_t)e, count, cu, ca, 0u);
+            lat[c] = nw;
+        } else {
+            *vabort = 1u;
+        }
+        if (count) {
+            // each consumer warp's counts into its own slot of the sample ring
+            // (summed over the four warps only when the ring is written out)
+            cu = __reduce_add_sync(0xFFFFFFFFu, cu);
+            ca = __reduce_add_sync(0xFFFFFFFFu, ca);
+            if ((c & 31u) == 0) {
+                if (rec) {
+                    wring[nring][c >> 5][0] = cu;
+                    wring[nring][c >> 5][1] = ca;
+                }
+                if (last) {  // the extra slot holds the state after the last sweep
+                    wring[kRingSamples][c >> 5][0] = cu;
+                    wring[kRingSamples][c >> 5][1] = ca;
+                }
+            }
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (*vabort) break;
+        if (p == 1u) {
+            if (rec) ++nring;
+            if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
+        }
+        if (nring == kRingSamples || s + 1 == nsteps) {
+            // the ring (at the end the rest of it) to global memory
+            for (uint32_t r = c; r < 2 * nring; r += kWsWords) {
+                const uint32_t q = r >> 1, j = r & 1u;
+                A.acc[2 * slot + r] = (unsigned long long)wring[q][0][j] + wring[q][1][j] + wring[q][2][j] +
+                                      wring[q][3][j];
+            }
+            slot += nring;
+            nring = 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // the ring is free again
+        }
+    }
+    if (*vabort) {
+        if (A.err && c == 0) atomicExch(A.err, 1u);
+        return;
+    }
+    if (c < 2)
+        A.acc[2 * A.nrec + c] = (unsigned long long)wring[kRingSamples][0][c] + wring[kRingSamples][1][c] +
+                                wring[kRingSamples][2][c] + wring[kRingSamples][3][c];
+    static_cast<uint32_t *>(A.spins)[c] = lat[c];
+}
+
 // The one-CTA kernel spread over a cluster of k = 2, 4 or 8 CTAs (distributed
 // shared memory): CTA c holds rows [c L/k, (c + 1) L/k) with one halo row above
 // and below.  At the start of each step it copies the halos from the
@@ -466,6 +649,9 @@ bool tiny_lattice_ok(uint64_t L) { return L >= 64 && L <= 1024 && (L & (L - 1)) 
 
 bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
+    if (c.proc_bits == kTinyProcBits && L == kTinyWsL && rows == L && c.block == kTinyWsBlock &&
+        c.rows_per_item == 1 && c.grid == 1 && c.regcap == 0 && c.insert == 0 && c.persistent == 0)
+        return true;  // the warp-specialised kernel
     return c.proc_bits == kTinyProcBits && tiny_lattice_ok(L) && rows == L && c.regcap == 0 && c.insert == 0 &&
            (c.block == 128 || c.block == 256 || c.block == 512) &&
            (c.rows_per_item == 1 || c.rows_per_item == 2 || c.rows_per_item == 4) &&
@@ -485,8 +671,15 @@ LaunchConfig plain_launch(const LaunchConfig &c)
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, uint32_t ctas,
                         cudaStream_t s)
 {
-    if (!tiny_lattice_ok(a.L) || a.nsweeps == 0 || block == 0 || block > kTinyMaxThreads || block % 32 != 0)
-        return cudaErrorInvalidValue;
+    if (!tiny_lattice_ok(a.L) || a.nsweeps == 0) return cudaErrorInvalidValue;
+    if (ctas == 1 && a.L == kTinyWsL && block == kTinyWsBlock && threads_per_word == 1) {
+        if (!a.use_field) {
+            k_tiny_ws<<<1, kTinyWsBlock, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        block = kTinyMaxThreads;  // in a field: the one-CTA field kernel (no warp-specialised form)
+    }
+    if (block == 0 || block > kTinyMaxThreads || block % 32 != 0) return cudaErrorInvalidValue;
     if (ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8) return cudaErrorInvalidValue;
     using TinyKernel = void (*)(TinyRunArgs);
     TinyKernel kern;

@@ -90,9 +90,14 @@ def test_tiny_is_rejected_where_it_does_not_apply(P):
         with pytest.raises(P.IsingError):
             lat.set_launch(**TINY, block=256, rows_per_item=1)
         lat.close()
+    lat = P.Lattice(128, 2.0, seed=1)
+    with pytest.raises(P.IsingError):
+        lat.set_launch(**TINY, block=1024, rows_per_item=1)
+    lat.close()
     lat = P.Lattice(64, 2.0, seed=1)
-    for bad in ({"block": 1024}, {"grid": 3}, {"grid": 16}, {"rows_per_item": 3}, {"rows_per_item": 8},
-                {"regcap": 1}):
+    # 1024 threads is the warp-specialised form, at L = 64 with one thread per word only
+    for bad in ({"block": 1024, "rows_per_item": 2}, {"block": 1024, "grid": 2}, {"grid": 3}, {"grid": 16},
+                {"rows_per_item": 3}, {"rows_per_item": 8}, {"regcap": 1}):
         cfg = dict(TINY, block=256, rows_per_item=1)
         cfg.update(bad)
         with pytest.raises(P.IsingError):
@@ -161,5 +166,63 @@ def test_tiny_cluster_bit_exact(P, orc, L, ctas, tpw):
     M3, E3 = lat.sweep(4, 1, collect=True)
     Mo3, Eo3 = orc.run_field(s, 4, seed, sid, T, 0.7, t0=n + 7)
     assert np.array_equal(M3, Mo3) and np.array_equal(E3, Eo3)
+    assert np.array_equal(lat.spins(), s)
+    lat.close()
+
+
+def test_warp_specialised_L64_is_bit_exact(P, orc):
+    """L = 64 with 1024 threads and one thread per word runs the warp-specialised
+    kernel (producer warps draw the masks into a ring, consumer warps update):
+    lattice and every sample against the oracle, for several call splits and
+    sample spacings, both parities of the start sweep and record_every = 0."""
+    L, T, seed, sid = 64, 2.269185, 17, 5
+    thr4, thr8 = orc.thresholds(T)
+    lat = P.Lattice(L, T, seed=seed, stream_id=sid, init="hot")
+    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=1, persistent=0)
+    s = orc.init_hot(L, seed, sid)
+    t = 0
+    for n, rec in ((1, 1), (7, 3), (300, 1), (129, 64), (5, 0), (1000, 7)):
+        got = lat.sweep(n, rec, collect=bool(rec))
+        Mo, Eo = orc.run(s, n, seed, sid, thr4, thr8, t0=t)
+        if rec:
+            k0 = (rec - 1 - t) % rec  # first recorded sweep of this call
+            assert np.array_equal(got[0], Mo[k0::rec]) and np.array_equal(got[1], Eo[k0::rec]), (n, rec)
+        assert (lat.measure()["M"], lat.measure()["E"]) == (Mo[-1], Eo[-1])
+        t += n
+    assert np.array_equal(lat.spins(), s)
+    lat.close()
+
+
+def test_warp_specialised_wait_runs_out_and_reports(P, monkeypatch):
+    """A step whose masks are never announced: the consumers' bounded wait runs
+    out, the call reports ISING_ERR_TIMEOUT, the handle is failed, and the GPU
+    stays usable."""
+    lat = P.Lattice(64, 2.0, seed=1, init="hot")
+    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=1, persistent=0)
+    monkeypatch.setenv("ISING_TINY_HOLD_STEP", "6")
+    with pytest.raises(P.IsingError) as ei:
+        lat.sweep(10, 1, collect=True)
+    assert ei.value.status == P.ERR_TIMEOUT
+    monkeypatch.delenv("ISING_TINY_HOLD_STEP")
+    with pytest.raises(P.IsingError) as ei:
+        lat.sweep(1, 1)
+    assert ei.value.status == P.ERR_STATE
+    lat.close()
+    ok = P.Lattice(64, 2.0, seed=1, init="hot")
+    ok.sweep(10, 1)
+    assert ok.measure()["sweeps_done"] == 10
+    ok.close()
+
+
+def test_warp_specialised_configuration_in_a_field_runs_the_field_kernel(P, orc):
+    """The warp-specialised configuration has no field form: in a field the
+    one-CTA field kernel runs instead, bit-exact with the oracle."""
+    L, T, H, seed = 64, 2.1, 0.3, 9
+    lat = P.Lattice(L, T, seed=seed, init="hot", H=H)
+    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=1, persistent=0)
+    M, E = lat.sweep(12, 1, collect=True)
+    s = orc.init_hot(L, seed, 0)
+    Mo, Eo = orc.run_field(s, 12, seed, 0, T, H)
+    assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
     assert np.array_equal(lat.spins(), s)
     lat.close()
