@@ -235,16 +235,21 @@ ISING_API const char *ising_last_error(void);
  * grid the CTAs: 1, or a thread-block cluster of 2, 4 or 8 CTAs that split
  * the rows and read their neighbours' boundary rows from distributed shared
  * memory, with a cluster barrier between the steps; regcap = insert = 0.  It is
- * the default for L <= 512 (one CTA at L = 64, a cluster of 8 above).  At
- * L = 64 the one-CTA configuration with block 512 and one thread per word is
- * warp-specialised: four warps update the words, twelve draw the acceptance
- * masks of later steps into a ring in shared memory, handed over through
- * mbarriers whose waits are bounded (when one runs out the call returns
- * ISING_ERR_TIMEOUT and the handle is failed; the environment variable
- * ISING_TINY_HOLD_STEP = 1 + a step index withholds that step's masks, for
- * failure-detection tests only).  In a field (H != 0) it uses one thread per
- * word whatever rows_per_item says; the step kernels are then replaced by the
- * field step kernel.
+ * the default for L <= 512 (the warp-specialised cluster form below at L = 64
+ * and 128, a cluster of 8 at 256 and 512).  At L = 64 and 128, block 1024 with one thread
+ * per word selects the warp-specialised form: L * L / 32 consumer threads keep
+ * the lattice in registers and update it, producer groups draw the acceptance
+ * masks of later steps into a ring of tagged entries in the consumers' shared
+ * memory, and mbarriers hand the ring slots back.  With grid 1 (L = 64 only)
+ * producers and consumers share one CTA; with grid 2, 4 or 8 the first CTA of
+ * a cluster holds the consumers and the other CTAs the producers, which store
+ * through distributed shared memory.  Every wait is bounded: when one runs out
+ * the call returns ISING_ERR_TIMEOUT and the handle is failed (the environment
+ * variable ISING_TINY_HOLD_STEP = 1 + a step index withholds that step's
+ * masks, for failure-detection tests only).  In a field (H != 0) it uses one
+ * thread per word whatever rows_per_item says, and the warp-specialised
+ * configurations run the one-CTA or cluster field kernel with block 512; the
+ * step kernels are then replaced by the field step kernel.
  * persistent = 1 (with proc_bits 32 or 64, insert 0, grid 0; regcap 0, 1 or
  * 2 = the compiler's choice, <= 40 or <= 64 registers)
  * runs every sweep of an ising_sweep call in one cooperative launch of that

@@ -43,9 +43,10 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
     }
     // untuned: the shapes the autotuner picked on GB300 at these sizes
     // (fields: proc_bits, regcap, insert, block, rows_per_item, grid)
-    // one CTA (L = 64) or a cluster of 8 CTAs (L = 128 .. 512): every sweep of a call in one launch
-    if (L == 64) return LaunchConfig{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 1};  // warp-specialised
-    if (L == 128) return LaunchConfig{kTinyProcBits, 0, 0, 128, 2, 8};
+    // every sweep of a call in one launch: the warp-specialised cluster kernel
+    // (L = 64: 4 CTAs, L = 128: 8 CTAs), a cluster of 8 CTAs (L = 256, 512)
+    if (L == 64) return LaunchConfig{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 4};
+    if (L == 128) return LaunchConfig{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 8};
     if (L == 256) return LaunchConfig{kTinyProcBits, 0, 0, 256, 1, 8};
     if (L == 512) return LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 8};
     if (L < 4096) return LaunchConfig{32, 1, 0, 256, 2, 0};
@@ -62,10 +63,10 @@ void remember_launch(int device, uint64_t L, uint32_t word_bits, const LaunchCon
 std::vector<LaunchConfig> launch_candidates(uint64_t L, uint64_t rows)
 {
     std::vector<LaunchConfig> out;
-    // the one-CTA kernel, for lattices one CTA holds (and its warp-specialised
-    // form at L = 64)
-    {
-        LaunchConfig ws{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 1};
+    // the one-CTA kernel, for lattices one CTA holds, and the warp-specialised
+    // forms at L = 64 and 128 (one CTA at L = 64, or a cluster)
+    for (uint32_t ctas : {1u, 2u, 4u, 8u}) {
+        LaunchConfig ws{kTinyProcBits, 0, 0, kTinyWsBlock, 1, ctas};
         if (launch_config_valid(ws, L, rows)) out.push_back(ws);
     }
     for (uint32_t ctas : {1u, 2u, 4u, 8u})

@@ -129,9 +129,11 @@ struct TinyRunArgs {
     // consumers' wait runs out (with a short wait limit)
     uint32_t hold_step;
 };
-// The warp-specialised one-CTA configuration: L = 64, 1024 threads, one thread
-// per word (tiny.cu): four warps update the words, 28 draw the masks.
-constexpr uint32_t kTinyWsL = 64, kTinyWsBlock = 1024;
+// The warp-specialised configurations (tiny.cu): L = 64 or 128, 1024 threads
+// per CTA, one thread per word; one CTA (L = 64: four consumer warps, 28
+// producer warps) or a cluster of 2, 4 or 8 CTAs (consumers in the first,
+// producers in the others).
+constexpr uint32_t kTinyWsBlock = 1024;
 // ctas = 1: one CTA; 2, 4, 8: a cluster of CTAs, each with L / ctas rows.
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, uint32_t ctas,
                         cudaStream_t s);

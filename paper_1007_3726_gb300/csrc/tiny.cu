@@ -255,28 +255,66 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Warp-specialised one-CTA kernel for L = 64 (128 words of 32 bits).  With one
-// SM for the whole lattice a step is short, and when every thread both draws
-// and updates, the dependent bit logic and the barrier of each step leave most
-// issue slots idle.  Here the roles are split:
-//   warps 0-3   consumers: thread c updates word c at every step (the bit logic
-//               with the masks read from shared memory, the store, the counts);
-//   warps 4-31  producers: seven groups of 128 threads; group g draws the masks
-//               of steps g, g + 7, g + 14, ... for word (thread index mod 128)
-//               into a ring of kWsSlots steps in shared memory (seven steps in
-//               flight give the Philox chains enough warps to hide their
-//               latency).
-// The masks do not depend on the spins, so the producers run ahead of the
-// consumers by up to kWsSlots steps.  A ring entry is one 64-bit word, the
-// masks and the tag s + 1 of their step, written with one store: the consumer
-// of word c spins on its entry until the tag is there (a shared-memory load,
-// short latency).  Having read it, the consumer arrives on the slot's "empty"
-// mbarrier; the producers wait on that mbarrier before they reuse the slot
-// (a suspended wait, so that waiting producers leave the issue slots to the
-// consumers).  A named barrier of the consumers ends each step.  Every wait is
-// bounded: when one runs out, the kernel sets `abort` (the consumers all stop
-// after the same barrier, the producers leave) and *err, so the kernel always
-// ends.
+// Warp-specialised kernels for L = 64 and L = 128 (a row is 2 or 4 words of
+// 32 bits).  A lattice this small leaves most of an SM's issue slots idle when
+// every thread both draws and updates: the dependent bit logic and the
+// barrier of each step are short, the Philox draws long.  The draws do not
+// depend on the spins, so the roles are split:
+//   consumers  one thread per 32-bit word (L * L / 32 threads in the first
+//              CTA).  The lattice stays in registers: the left and right
+//              neighbour words and the rows above and below come from other
+//              lanes by warp shuffles, the rows across a warp boundary through
+//              a small shared-memory array.  A step is the ring entry, the bit
+//              logic, one store of the word's boundary row (lanes off a warp
+//              boundary store to a scratch slot) and one barrier of the
+//              consumers; on a counted sweep the second step also stores the
+//              new word, tagged, into a snapshot ring.  The step has no branch
+//              but one that is taken only when something has to wait (the
+//              ring entry is not there yet, a snapshot slot is still being
+//              read) or a failure is to be acted on.
+//   arriver    one thread next to the consumers: it follows their progress
+//              (thread 0 of the consumers publishes each finished step) and
+//              frees each step's ring slot with one arrival on the slot's
+//              mbarrier;
+//   counters   a few warps; counter k takes every few counted sweeps starting
+//              with the k-th: once all tags of the sweep's snapshot are there
+//              it takes M and E of the whole lattice from it, writes the
+//              sample and frees the snapshot slot.  No remote arrival, global
+//              store or count is then on the consumers' path.
+//   producers  groups of L * L / 32 threads; a group draws the masks of every
+//              NG-th step (NG groups in all) and writes them, tagged with the
+//              step, into the group's slot of the consumers' ring: one 64-bit
+//              entry (step + 1) << 32 | masks per word.  It draws the masks of
+//              its next step first and then waits until the slot's previous
+//              entry has been freed, so the draws overlap the wait.
+// Two forms:
+//   CL = false  one CTA of 1024 threads for L = 64: 128 consumer threads, the
+//               arriving thread, two counter warps and six producer groups;
+//   CL = true   a thread-block cluster of C CTAs of 1024 threads: CTA 0 holds
+//               the consumers, the arriving thread and four counter warps,
+//               CTAs 1 .. C - 1 the producers (1024 / (L L / 32) groups each),
+//               which store into CTA 0's ring through distributed shared
+//               memory; the arrival goes to the slot's mbarrier in the
+//               producing CTA.  The producers' issue
+//               slots then no longer compete with the consumers', and C - 1
+//               SMs draw.
+// Ordering.  A consumer's load of a ring entry has returned its value before
+// the consumer reaches the barrier that ends the step (the value feeds the
+// boundary store that precedes it); thread 0 publishes the step after that
+// barrier, the arriving thread arrives for the slot after it has read the publication,
+// and a producer stores into the slot only after its wait has seen the
+// arrival.  Each link follows the completion of the one before, so no store
+// into a slot can overtake a load of its previous entry; the arrivals and the
+// publication are relaxed (a release at cluster scope would fence every
+// thread's memory operations at every step).  Snapshot entries carry their
+// sweep's tag, and a counter reads one only once the tag is there.
+// Failure.  Every wait is bounded.  A consumer whose wait runs out sets the
+// abort flag of its step's parity before the step's barrier; every consumer
+// reads that flag after the barrier and before the next one, so all of them
+// stop at the same point.  The arriving thread, the counters and the producers stop when their own
+// waits run out; any of them sets *err, so the kernel always ends.  In the
+// cluster form every thread reaches a final cluster barrier, so no CTA leaves
+// while another may still use its shared memory.
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -285,156 +323,413 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+
+constexpr uint32_t kWsSpinLimit = 1u << 24;  // polls of a consumer's wait before it gives up
+constexpr uint32_t kWsWaitLimit = 1u << 20;  // polls of a producer's mbarrier wait
+constexpr uint32_t kWsMaxGroups = 7 * (kTinyWsBlock / 128);  // L = 64 on a cluster of 8
+constexpr uint32_t kWsSnaps = 8;             // counted sweeps the consumers may run ahead of the counters
+
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank)
 {
-    // the state token goes to the sink: no register waits for the arrival
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
 }
-// Waits (bounded: at most `limit` polls, each of which may suspend the thread
-// for a while without using issue slots) until the phase of the given parity
-// has completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
+__device__ __forceinline__ uint32_t cluster_rank()
 {
-    const uint32_t a = smem_addr(bar);
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// A ring entry: written by a producer of this CTA (CL = false) or of another
+// CTA of the cluster (CL = true), read by the consumers.
+template <bool CL>
+__device__ __forceinline__ void ring_store(uint32_t addr, uint64_t v)
+{
+    if constexpr (CL)
+        asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+    else
+        asm volatile("st.volatile.shared.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+template <bool CL>
+__device__ __forceinline__ uint64_t ring_load(uint32_t addr)
+{
+    uint64_t v;
+    if constexpr (CL)
+        asm volatile("ld.relaxed.cluster.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+    else
+        asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_volatile_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_volatile_u64(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+// The arriving thread's arrival on a slot's mbarrier (in the producing CTA when CL).
+template <bool CL>
+__device__ __forceinline__ void slot_arrive(uint32_t addr)
+{
+    if constexpr (CL)
+        asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+    else
+        asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+// A producer's bounded wait until the phase of the given parity of its slot's
+// mbarrier has completed.
+template <bool CL>
+__device__ __forceinline__ bool slot_wait(uint32_t addr, uint32_t parity, uint32_t limit)
+{
     for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done)
-                     : "r"(a), "r"(parity)
-                     : "memory");
+        if constexpr (CL)
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.relaxed.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(done)
+                         : "r"(addr), "r"(parity)
+                         : "memory");
+        else
+            asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.relaxed.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(done)
+                         : "r"(addr), "r"(parity)
+                         : "memory");
         if (done) return true;
     }
     return false;
 }
 
-constexpr uint32_t kWsSlots = 8;
-constexpr uint32_t kWsWords = 128;
-constexpr uint32_t kWsGroups = kTinyWsBlock / kWsWords - 1;  // producer groups (7)
-constexpr uint32_t kWsSpinLimit = 1u << 24;  // polls of a consumer's wait before it gives up
-constexpr uint32_t kWsWaitLimit = 1u << 20;  // polls of a producer's mbarrier wait
-
-__global__ void __launch_bounds__(kTinyWsBlock) k_tiny_ws(const __grid_constant__ TinyRunArgs A)
+// The bit logic of update_word32_drawn for one 32-bit word (all 4 bytes).
+__device__ __forceinline__ uint32_t ws_update_word(uint32_t cur, uint32_t up, uint32_t dn, uint32_t lw, uint32_t rw,
+                                                   uint32_t off, uint32_t pk)
 {
-    __shared__ uint32_t lat[kWsWords];
-    __shared__ uint64_t entries[kWsSlots][kWsWords];  // (step + 1) << 32 | masks
-    __shared__ __align__(8) uint64_t empty[kWsSlots];  // 128 consumer arrivals: the slot is read
-    // per consumer warp (+1 spins, anti-aligned bonds) of up to kRingSamples
-    // samples, and of the state after the last sweep
-    __shared__ unsigned int wring[kRingSamples + 1][4][2], ws_abort;
-    volatile uint64_t *const ve = &entries[0][0];
-    volatile unsigned int *const vabort = &ws_abort;
+    constexpr uint32_t even = 0x55555555u;
+    const uint32_t left = __funnelshift_l(lw, cur, 1);   // (cur << 1) | (lw >> 31): site x - 1
+    const uint32_t right = __funnelshift_r(cur, rw, 1);  // (cur >> 1) | (rw << 31): site x + 1
+    const uint32_t i1 = cur ^ up, i2 = cur ^ dn, i3 = cur ^ left, i4 = cur ^ right;
+    const uint32_t s12 = i1 ^ i2, c12 = i1 & i2;
+    const uint32_t s34 = i3 ^ i4, c34 = i3 & i4;
+    const uint32_t odd = s12 ^ s34;
+    const uint32_t ge2 = c12 | c34 | (s12 & s34);
+    const uint32_t eq1 = odd & ~ge2;
+    const uint32_t eq0 = ~(odd | ge2);
+    const uint32_t p4 = (pk & even) << off;
+    const uint32_t p8 = ((pk >> 1) & even) << off;
+    return cur ^ ((even << off) & (ge2 | (eq1 & p4) | (eq0 & p8)));
+}
+
+template <uint32_t V>
+struct WsParity {
+    static constexpr uint32_t value = V;
+};
+
+template <uint32_t LL, bool CL>
+__global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant__ TinyRunArgs A)
+{
+    constexpr uint32_t W = LL / 32;              // words per row
+    constexpr uint32_t NWORDS = LL * W;          // consumer threads, threads of a producer group
+    constexpr uint32_t NCW = NWORDS / 32;        // consumer warps
+    constexpr uint32_t GPC = kTinyWsBlock / NWORDS;  // producer groups per producer CTA
+    constexpr uint32_t NCOUNT = CL ? 4 : 2;      // counter warps
+    // CL = false: producer groups beside the consumers, the arriving thread's
+    // warp and the counter warps, and the threads left over
+    constexpr uint32_t GLOCAL = (kTinyWsBlock - NWORDS - 32 - 32 * NCOUNT) / NWORDS;
+    constexpr uint32_t IDLE = CL ? 0 : kTinyWsBlock - NWORDS - 32 - 32 * NCOUNT - GLOCAL * NWORDS;
+    constexpr uint32_t kStopped = 0xFFFFFFFFu;
+    constexpr uint32_t NB = 2 * NCW * W;         // boundary rows; then one scratch slot per consumer
+    static_assert(CL || LL == 64, "the one-CTA form is for L = 64");
+    extern __shared__ __align__(16) uint64_t ring[];  // [NG][NWORDS], in CTA 0
+    __shared__ __align__(8) uint64_t empty[kWsMaxGroups];  // per slot: one arrival frees it
+    __shared__ uint32_t bnd[NB + NWORDS];  // first rows of the consumer warps, last rows, scratch
+    // snapshots (sweep tag << 32 | word) of the lattice after counted sweeps, and a scratch row
+    __shared__ __align__(8) uint64_t snap[kWsSnaps + 1][NWORDS];
+    // per snapshot slot: how many snapshots the counter warps have read from it
+    __shared__ uint32_t slot_read[kWsSnaps];
+    __shared__ uint32_t done_step, abort_flag[2];
     const uint32_t tid = threadIdx.x;
-    const uint32_t L = kTinyWsL, W = 2, nsteps = 2 * A.nsweeps;
-    const uint64_t groups_per_row = L >> 3;
+    const uint32_t rank = CL ? cluster_rank() : 0u;
+    const uint32_t NG = CL ? GPC * (gridDim.x - 1) : GLOCAL;
+    const uint32_t nsteps = 2 * A.nsweeps;
     // a held step (failure testing) runs the waits out quickly
     const uint32_t limit = A.hold_step ? (1u << 14) : kWsSpinLimit;
     const uint32_t plimit = A.hold_step ? (1u << 12) : kWsWaitLimit;
-    const uint32_t *src = static_cast<const uint32_t *>(A.spins);
-    if (tid < kWsWords) {
-        lat[tid] = src[tid];
-        for (uint32_t k = 0; k < kWsSlots; ++k) entries[k][tid] = 0ull;
+    if (rank == 0) {
+        for (uint32_t i = tid; i < NG * NWORDS; i += kTinyWsBlock) ring[i] = 0ull;
+        for (uint32_t i = tid; i < kWsSnaps * NWORDS; i += kTinyWsBlock) (&snap[0][0])[i] = 0ull;
     }
     if (tid == 0) {
-        ws_abort = 0u;
-        for (uint32_t k = 0; k < kWsSlots; ++k) mbar_init(&empty[k], kWsWords);
+        for (uint32_t k = 0; k < NG; ++k) mbar_init(&empty[k], 1u);
+        done_step = 0u;
+        for (uint32_t k = 0; k < kWsSnaps; ++k) slot_read[k] = 0u;
+        abort_flag[0] = 0u;
+        abort_flag[1] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();  // the last barrier of the whole block
+    if constexpr (CL)
+        cluster_barrier();  // rings and mbarriers of every CTA ready
+    else
+        __syncthreads();
 
-    HalfSweepArgs a;
-    a.key = A.key;
-    a.thr4 = A.thr4;
-    a.thr8 = A.thr8;
-    a.zero = 0u;
-    if (tid >= kWsWords) {
-        // ---- producers
-        const uint32_t pt = tid - kWsWords, grp = pt / kWsWords, w = pt % kWsWords;
-        const uint64_t g = (uint64_t)(w >> 1) * groups_per_row + (uint64_t)(w & 1u) * 4u;
-        for (uint32_t s = grp; s < nsteps; s += kWsGroups) {
-            const uint32_t k = s % kWsSlots;
-            if (s >= kWsSlots && !mbar_wait(&empty[k], ((s / kWsSlots) & 1u) ^ 1u, plimit)) {
-                // the consumers did not read the slot's previous entry in time
-                *vabort = 1u;
-                if (A.err) atomicExch(A.err, 1u);
-                return;
-            }
+    const bool consumer = rank == 0 && tid < NWORDS;
+    const bool arriver = rank == 0 && tid == NWORDS;
+    const bool counter = rank == 0 && tid >= NWORDS + 32 && tid < NWORDS + 32 + 32 * NCOUNT;
+    const bool producer = CL ? rank != 0 : (tid >= NWORDS + 32 + 32 * NCOUNT && tid < kTinyWsBlock - IDLE);
+    if (producer) {
+        HalfSweepArgs a;
+        a.key = A.key;
+        a.thr4 = A.thr4;
+        a.thr8 = A.thr8;
+        a.zero = 0u;
+        const uint32_t pt = CL ? tid : tid - NWORDS - 32 - 32 * NCOUNT;
+        const uint32_t G = (CL ? (rank - 1) * GPC : 0u) + pt / NWORDS, w = pt % NWORDS;
+        const uint64_t g = (uint64_t)(w / W) * (LL >> 3) + (uint64_t)(w % W) * 4u;
+        const uint32_t dst = CL ? mapa_shared(smem_addr(&ring[G * NWORDS + w]), 0u) : smem_addr(&ring[G * NWORDS + w]);
+        const uint32_t slot_bar = smem_addr(&empty[G]);
+        for (uint32_t s = G; s < nsteps; s += NG) {
             tiny_step_values(a, A, A.t0 + (s >> 1), s & 1u);
             uint32_t h4[1], h8[1];
             word_draw_masks<4, 0, 4>(a, a, g, h4, h8);
+            // the slot's previous entry (step s - NG) must have been freed
+            if (s >= NG && !slot_wait<CL>(slot_bar, ((s / NG) & 1u) ^ 1u, plimit)) {
+                if (A.err) atomicExch(A.err, 1u);
+                break;
+            }
             if (A.hold_step == s + 1) continue;  // never published (failure testing)
-            ve[k * kWsWords + w] = ((uint64_t)(s + 1) << 32) | pack_masks(h4[0], h8[0]);
+            ring_store<CL>(dst, ((uint64_t)(s + 1) << 32) | pack_masks(h4[0], h8[0]));
         }
-        return;
-    }
-    // ---- consumers: thread c updates word c (row c / 2, word c % 2).  A step
-    // ends with a named barrier of the 128 consumers (bar.sync 1, 128); no
-    // consumer leaves the loop alone, so every barrier completes.
-    const uint32_t c = tid, y = c >> 1, w = c & 1u;
-    const uint32_t row = c - w;
-    const uint32_t iu = (y == 0 ? kWsWords - W : row - W) + w, id = (y + 1 == L ? 0u : row + W) + w;
-    const uint32_t inb = row + (w ^ 1u);  // W = 2: the left and the right neighbour word
-    uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;
-    uint32_t slot = 0, nring = 0;
-    for (uint32_t s = 0; s < nsteps; ++s) {
-        const uint32_t k = s % kWsSlots, p = s & 1u;
-        const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
-        const bool last = (s >> 1) + 1 == A.nsweeps;
-        const bool count = p == 1u && (rec || last);
-        unsigned int cu = 0, ca = 0;
-        uint64_t e = ve[k * kWsWords + c];
-        uint32_t i = 0;
-        while ((uint32_t)(e >> 32) != s + 1 && ++i < limit) e = ve[k * kWsWords + c];
-        if ((uint32_t)(e >> 32) == s + 1) {
-            mbar_arrive(&empty[k]);  // this thread has read the slot (release: after the load)
-            const uint32_t nw = update_word32_drawn<4>(lat[c], lat[iu], lat[id], lat[inb], lat[inb], (y + p) & 1u,
-                                                       (uint32_t)e, count, cu, ca, 0u);
-            lat[c] = nw;
-        } else {
-            *vabort = 1u;
-        }
-        if (count) {
-            // each consumer warp's counts into its own slot of the sample ring
-            // (summed over the four warps only when the ring is written out)
-            cu = __reduce_add_sync(0xFFFFFFFFu, cu);
-            ca = __reduce_add_sync(0xFFFFFFFFu, ca);
-            if ((c & 31u) == 0) {
-                if (rec) {
-                    wring[nring][c >> 5][0] = cu;
-                    wring[nring][c >> 5][1] = ca;
+    } else if (consumer) {
+        // thread c holds word c: row c / W, word c % W
+        const uint32_t c = tid, q = c >> 5, l = c & 31u, w = c % W;
+        const uint32_t row_off = (c / W) & 1u;  // parity of the row
+        const uint32_t lane_l = (l & ~(W - 1u)) | ((w + W - 1u) & (W - 1u));
+        const uint32_t lane_r = (l & ~(W - 1u)) | ((w + 1u) & (W - 1u));
+        const uint32_t qu = (q + NCW - 1u) % NCW, qd = (q + 1u) % NCW;
+        const bool top = l < W, bottom = l >= 32u - W;
+        // this word's boundary slot (first row, last row or scratch), and the
+        // slots of the row above a warp's first row and below its last row
+        const uint32_t my_b = top ? q * W + w : bottom ? NCW * W + q * W + w : NB + c;
+        const uint32_t up_b = NCW * W + qu * W + w, dn_b = qd * W + w;
+        uint32_t v = static_cast<const uint32_t *>(A.spins)[c];
+        bnd[my_b] = v;
+        asm volatile("bar.sync 1, %0;" ::"r"(NWORDS) : "memory");  // the initial boundary rows
+        const uint32_t ring0 = smem_addr(&ring[c]);
+        const uint32_t abort0 = smem_addr(&abort_flag[0]);
+        const uint32_t sread0 = smem_addr(&slot_read[0]);
+        const uint32_t done_addr = smem_addr(&done_step);
+        uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;
+        uint32_t G = 0, s = 0, cidx = 0, sread = 0;
+        bool stop = false;
+
+        // one step of parity p; false when the consumers stop
+        auto step = [&](auto pc, bool counted) -> bool {
+            constexpr uint32_t p = decltype(pc)::value;
+            const uint32_t ea = ring0 + G * (NWORDS * 8u);
+            uint64_t e = ring_load<CL>(ea);
+            const uint32_t vl = __shfl_sync(0xFFFFFFFFu, v, lane_l);
+            const uint32_t vr = W == 2 ? vl : __shfl_sync(0xFFFFFFFFu, v, lane_r);
+            const uint32_t su = __shfl_up_sync(0xFFFFFFFFu, v, W);
+            const uint32_t sd = __shfl_down_sync(0xFFFFFFFFu, v, W);
+            const uint32_t bu = bnd[up_b], bd = bnd[dn_b];
+            // set (before the previous barrier) by a consumer whose wait ran out
+            const uint32_t ab = ld_volatile_u32(abort0 + 4u * (p ^ 1u));
+            const uint32_t tag = s + 1u;
+            const uint32_t sslot = cidx % kWsSnaps, sneed = cidx / kWsSnaps;
+            // the snapshot slot of this sweep: read by the counters as often as
+            // it has been written (loaded at the sweep's first step, checked at
+            // its second, where the snapshot is stored)
+            if constexpr (p == 0u) sread = ld_volatile_u32(sread0 + 4u * sslot);
+            const bool snap_wait = p == 1u && counted && sread < sneed;
+            if (((uint32_t)(e >> 32) != tag) | (ab != 0u) | snap_wait) {
+                if (ab != 0u) return false;  // every consumer has read the same flag
+                bool fail = false;
+                for (uint32_t n = 0; (uint32_t)(e >> 32) != tag; ++n) {
+                    if (n >= limit) {
+                        fail = true;
+                        break;
+                    }
+                    e = ring_load<CL>(ea);
                 }
-                if (last) {  // the extra slot holds the state after the last sweep
-                    wring[kRingSamples][c >> 5][0] = cu;
-                    wring[kRingSamples][c >> 5][1] = ca;
+                // the snapshot slot's previous snapshot must have been read
+                for (uint32_t m = 0; snap_wait && sread < sneed; ++m) {
+                    if (m >= limit) {
+                        fail = true;
+                        break;
+                    }
+                    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(sread) : "r"(sread0 + 4u * sslot) : "memory");
                 }
+                if (fail) abort_flag[p] = 1u;
             }
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (*vabort) break;
-        if (p == 1u) {
-            if (rec) ++nring;
+            const uint32_t vu = top ? bu : su, vd = bottom ? bd : sd;
+            v = ws_update_word(v, vu, vd, vl, vr, row_off ^ p, (uint32_t)e);
+            bnd[my_b] = v;
+            if constexpr (p == 1u) {
+                // counted sweep: the snapshot slot; otherwise the scratch row
+                const uint32_t k = counted ? sslot : kWsSnaps;
+                snap[k][c] = ((uint64_t)(cidx + 1u) << 32) | v;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(NWORDS) : "memory");
+            // every consumer is done with step s: thread 0 publishes it
+            asm volatile("{\n\t.reg .pred q;\n\tsetp.eq.u32 q, %0, 0;\n\t@q st.volatile.shared.u32 [%1], %2;\n\t}" ::"r"(c),
+                         "r"(done_addr), "r"(tag)
+                         : "memory");
+            G = G + 1u == NG ? 0u : G + 1u;
+            ++s;
+            return true;
+        };
+        auto sweep_counted = [&]() {
+            const bool counted = (A.record_every != 0u && phase + 1 == A.record_every);
             if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
-        }
-        if (nring == kRingSamples || s + 1 == nsteps) {
-            // the ring (at the end the rest of it) to global memory
-            for (uint32_t r = c; r < 2 * nring; r += kWsWords) {
-                const uint32_t q = r >> 1, j = r & 1u;
-                A.acc[2 * slot + r] = (unsigned long long)wring[q][0][j] + wring[q][1][j] + wring[q][2][j] +
-                                      wring[q][3][j];
+            return counted;
+        };
+        uint32_t i = 0;
+        for (; i + 2 <= A.nsweeps; i += 2) {
+            const bool c0 = sweep_counted() || i + 1 == A.nsweeps;
+            const bool c1 = sweep_counted() || i + 2 == A.nsweeps;
+            if (!step(WsParity<0>{}, c0) || !step(WsParity<1>{}, c0)) {
+                stop = true;
+                break;
             }
-            slot += nring;
-            nring = 0;
-            asm volatile("bar.sync 1, 128;" ::: "memory");  // the ring is free again
+            if (c0) ++cidx;
+            if (!step(WsParity<0>{}, c1) || !step(WsParity<1>{}, c1)) {
+                stop = true;
+                break;
+            }
+            if (c1) ++cidx;
+        }
+        if (!stop && i < A.nsweeps) {  // an odd number of sweeps: the last one
+            const bool c0 = true;      // the last sweep is always counted
+            (void)sweep_counted();
+            if (!step(WsParity<0>{}, c0) || !step(WsParity<1>{}, c0))
+                stop = true;
+            else
+                ++cidx;
+        }
+        // a wait that ran out in the last step (its flag was set before the
+        // last barrier, and nobody writes a flag after it)
+        if (!stop && (ld_volatile_u32(abort0) | ld_volatile_u32(abort0 + 4u)) != 0u) stop = true;
+        if (stop) {
+            if (c == 0) {
+                asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(done_addr), "r"(kStopped) : "memory");
+                if (A.err) atomicExch(A.err, 1u);
+            }
+        } else {
+            static_cast<uint32_t *>(A.spins)[c] = v;
+        }
+    } else if (arriver) {
+        // frees each finished step's ring slot: one arrival on the slot's
+        // mbarrier (in the producing CTA when CL)
+        const uint32_t done_addr = smem_addr(&done_step);
+        uint32_t next = 0, G = 0, n = 0;
+        while (next < nsteps) {
+            const uint32_t d = ld_volatile_u32(done_addr);
+            if (d == kStopped) break;
+            if (d <= next) {
+                if (++n >= 4 * limit) {  // longer than a consumer's wait: the consumers report first
+                    if (A.err) atomicExch(A.err, 1u);
+                    break;
+                }
+                continue;
+            }
+            n = 0;
+            do {
+                const uint32_t bar = smem_addr(&empty[G]);
+                slot_arrive<CL>(CL ? mapa_shared(bar, 1u + G / GPC) : bar);
+                G = G + 1u == NG ? 0u : G + 1u;
+            } while (++next < d);
+        }
+    } else if (counter) {
+        // counter warp k takes the counted sweeps k, k + NCOUNT, ...: M and E
+        // of the whole lattice from the sweep's snapshot, once all its tags
+        // are there.  Lane j holds words j, j + 32, ... (R of them); the word to
+        // the right is in the same row of the same lane group, the word below
+        // W lanes on (or, for the last rows of a group, in the next group).
+        constexpr uint32_t R = NWORDS / 32;
+        const uint32_t k = (tid - NWORDS - 32) >> 5, hl = tid & 31u;
+        const uint32_t re = A.record_every;
+        const uint32_t first = re ? (re - (A.t0 % re + 1u) % re) % re : 0u;  // first recorded sweep
+        const bool last_rec = re != 0u && A.nrec != 0u && first + (A.nrec - 1u) * re + 1u == A.nsweeps;
+        const uint32_t ncounted = A.nrec + (last_rec ? 0u : 1u);
+        const uint32_t lane_r = (hl & ~(W - 1u)) | ((hl + 1u) & (W - 1u));
+        const uint32_t lane_d = (hl + W) & 31u;
+        const uint32_t done_addr = smem_addr(&done_step);
+        for (uint32_t cidx = k; cidx < ncounted; cidx += NCOUNT) {
+            const uint32_t ks = cidx % kWsSnaps, want = cidx + 1u;
+            uint32_t x[R];
+            uint32_t n = 0, seen = 0;
+            bool ok = false, quit = false;
+            for (;;) {
+                bool all = true;
+#pragma unroll
+                for (uint32_t m = 0; m < R; ++m) {
+                    const uint64_t e = ld_volatile_u64(smem_addr(&snap[ks][hl + 32u * m]));
+                    x[m] = (uint32_t)e;
+                    all &= (uint32_t)(e >> 32) == want;
+                }
+                if (__all_sync(0xFFFFFFFFu, all)) {
+                    ok = true;
+                    break;
+                }
+                // not there yet: the wait runs out only while the consumers make
+                // no progress (a snapshot may be many sweeps away)
+                uint32_t d = hl == 0 ? ld_volatile_u32(done_addr) : 0u;
+                d = __shfl_sync(0xFFFFFFFFu, d, 0);
+                if (d == kStopped) {
+                    quit = true;
+                    break;
+                }
+                n = d != seen ? 0u : n + 1u;
+                seen = d;
+                if (n >= 4 * limit) break;
+                __nanosleep(64);
+            }
+            if (quit) break;
+            if (!ok) {
+                if (A.err && hl == 0) atomicExch(A.err, 1u);
+                break;
+            }
+            uint32_t part = 0;  // packed: up spins <= 16384, anti-aligned bonds <= 32768
+#pragma unroll
+            for (uint32_t m = 0; m < R; ++m) {
+                const uint32_t xr = __shfl_sync(0xFFFFFFFFu, x[m], lane_r);  // the word to the right
+                const uint32_t dn_same = __shfl_sync(0xFFFFFFFFu, x[m], lane_d);
+                const uint32_t dn_next = __shfl_sync(0xFFFFFFFFu, x[(m + 1u) % R], lane_d);
+                const uint32_t xd = hl + W < 32u ? dn_same : dn_next;  // the word below
+                const uint32_t right = __funnelshift_r(x[m], xr, 1);    // site x + 1
+                part += __popc(x[m]) + ((uint32_t)(__popc(x[m] ^ right) + __popc(x[m] ^ xd)) << 16);
+            }
+            const uint32_t sum = __reduce_add_sync(0xFFFFFFFFu, part);
+            if (hl == 0) {
+                const unsigned long long c0 = sum & 0xFFFFu, c1 = sum >> 16;
+                const bool rec = cidx < A.nrec;
+                const bool last = !rec || first + cidx * re + 1u == A.nsweeps;
+                if (rec) {
+                    A.acc[2 * cidx] = c0;
+                    A.acc[2 * cidx + 1] = c1;
+                }
+                if (last) {
+                    A.acc[2 * A.nrec] = c0;
+                    A.acc[2 * A.nrec + 1] = c1;
+                }
+            }
+            __syncwarp();  // every lane has read the snapshot
+            if (hl == 0)
+                asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_addr(&slot_read[ks])),
+                             "r"(cidx / kWsSnaps + 1u)
+                             : "memory");
         }
     }
-    if (*vabort) {
-        if (A.err && c == 0) atomicExch(A.err, 1u);
-        return;
-    }
-    if (c < 2)
-        A.acc[2 * A.nrec + c] = (unsigned long long)wring[kRingSamples][0][c] + wring[kRingSamples][1][c] +
-                                wring[kRingSamples][2][c] + wring[kRingSamples][3][c];
-    static_cast<uint32_t *>(A.spins)[c] = lat[c];
+    if constexpr (CL) cluster_barrier();  // no CTA leaves while another may still use its shared memory
 }
 
 // The one-CTA kernel spread over a cluster of k = 2, 4 or 8 CTAs (distributed
@@ -649,9 +944,10 @@ bool tiny_lattice_ok(uint64_t L) { return L >= 64 && L <= 1024 && (L & (L - 1)) 
 
 bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
-    if (c.proc_bits == kTinyProcBits && L == kTinyWsL && rows == L && c.block == kTinyWsBlock &&
-        c.rows_per_item == 1 && c.grid == 1 && c.regcap == 0 && c.insert == 0 && c.persistent == 0)
-        return true;  // the warp-specialised kernel
+    if (c.proc_bits == kTinyProcBits && (L == 64 || L == 128) && rows == L && c.block == kTinyWsBlock &&
+        c.rows_per_item == 1 && c.regcap == 0 && c.insert == 0 && c.persistent == 0)
+        // the warp-specialised kernels: one CTA (L = 64) or a cluster of 2, 4 or 8
+        return (c.grid == 1 && L == 64) || c.grid == 2 || c.grid == 4 || c.grid == 8;
     return c.proc_bits == kTinyProcBits && tiny_lattice_ok(L) && rows == L && c.regcap == 0 && c.insert == 0 &&
            (c.block == 128 || c.block == 256 || c.block == 512) &&
            (c.rows_per_item == 1 || c.rows_per_item == 2 || c.rows_per_item == 4) &&
@@ -668,16 +964,50 @@ LaunchConfig plain_launch(const LaunchConfig &c)
     return LaunchConfig{32, 1, 0, 256, 2, 0};  // the step shape of small lattices
 }
 
+// The warp-specialised kernels (L = 64 or 128): one CTA for L = 64, else a
+// cluster of `ctas` CTAs whose first CTA holds the consumers.
+static cudaError_t launch_tiny_ws(const TinyRunArgs &a, uint32_t ctas, cudaStream_t s)
+{
+    const uint32_t nwords = (uint32_t)(a.L * a.L / 32);
+    const uint32_t gpc = kTinyWsBlock / nwords;
+    if (ctas == 1) {
+        if (a.L != 64) return cudaErrorInvalidValue;
+        // the producer groups beside the consumers, the arriving thread's warp
+        // and the two counter warps
+        const size_t smem = (size_t)((kTinyWsBlock - nwords - 32 - 64) / nwords) * nwords * 8;
+        k_tiny_wsc<64, false><<<1, kTinyWsBlock, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    if (ctas != 2 && ctas != 4 && ctas != 8) return cudaErrorInvalidValue;
+    using TinyKernel = void (*)(TinyRunArgs);
+    const TinyKernel kern = a.L == 64 ? k_tiny_wsc<64, true> : k_tiny_wsc<128, true>;
+    const size_t smem = (size_t)gpc * (ctas - 1) * nwords * 8;  // one slot per producer group
+    // the static arrays (up to 40 KB at L = 128) and the ring together may
+    // pass the 48 KB that need no opt-in
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(kTinyWsBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = ctas;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, uint32_t ctas,
                         cudaStream_t s)
 {
     if (!tiny_lattice_ok(a.L) || a.nsweeps == 0) return cudaErrorInvalidValue;
-    if (ctas == 1 && a.L == kTinyWsL && block == kTinyWsBlock && threads_per_word == 1) {
-        if (!a.use_field) {
-            k_tiny_ws<<<1, kTinyWsBlock, 0, s>>>(a);
-            return cudaGetLastError();
-        }
-        block = kTinyMaxThreads;  // in a field: the one-CTA field kernel (no warp-specialised form)
+    if ((a.L == 64 || a.L == 128) && block == kTinyWsBlock && threads_per_word == 1) {
+        if (!a.use_field) return launch_tiny_ws(a, ctas, s);
+        block = kTinyMaxThreads;  // in a field: the field kernels (no warp-specialised form)
     }
     if (block == 0 || block > kTinyMaxThreads || block % 32 != 0) return cudaErrorInvalidValue;
     if (ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8) return cudaErrorInvalidValue;

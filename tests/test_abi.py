@@ -131,9 +131,13 @@ def test_launch_candidates_are_listed_without_a_gpu(ising):
     assert {x["proc_bits"] for x in c} == {32, 64}
     assert all(32768 % x["rows_per_item"] == 0 for x in c)
     assert len(ising.ising_launch_candidates(192)) >= 162
-    # the one-CTA kernel is a candidate exactly for power-of-two L <= 1024
-    for L, k in ((64, 36), (256, 36), (1024, 36), (192, 0), (2048, 0), (32768, 0)):
-        assert sum(x["proc_bits"] == 8 for x in ising.ising_launch_candidates(L)) == k, L
+    # the one-CTA kernel is a candidate exactly for power-of-two L <= 1024, its
+    # warp-specialised forms (block 1024) at L = 64 (grid 1, 2, 4, 8) and 128
+    # (grid 2, 4, 8)
+    for L, k, ws in ((64, 40, 4), (128, 39, 3), (256, 36, 0), (1024, 36, 0), (192, 0, 0), (2048, 0, 0),
+                     (32768, 0, 0)):
+        tiny = [x for x in ising.ising_launch_candidates(L) if x["proc_bits"] == 8]
+        assert len(tiny) == k and sum(x["block"] == 1024 for x in tiny) == ws, L
     # L = 2^20: configurations whose item count does not fit 32 bits are left out
     big = ising.ising_launch_candidates(2 ** 20)
     assert 0 < len(big) < len(c)

@@ -95,9 +95,10 @@ def test_tiny_is_rejected_where_it_does_not_apply(P):
         lat.set_launch(**TINY, block=1024, rows_per_item=1)
     lat.close()
     lat = P.Lattice(64, 2.0, seed=1)
-    # 1024 threads is the warp-specialised form, at L = 64 with one thread per word only
-    for bad in ({"block": 1024, "rows_per_item": 2}, {"block": 1024, "grid": 2}, {"grid": 3}, {"grid": 16},
-                {"rows_per_item": 3}, {"rows_per_item": 8}, {"regcap": 1}):
+    # 1024 threads is the warp-specialised form: L = 64 or 128, one thread per
+    # word, one CTA (L = 64 only) or a cluster of 2, 4 or 8
+    for bad in ({"block": 1024, "rows_per_item": 2}, {"block": 1024, "grid": 3}, {"block": 1024, "grid": 16},
+                {"grid": 3}, {"grid": 16}, {"rows_per_item": 3}, {"rows_per_item": 8}, {"regcap": 1}):
         cfg = dict(TINY, block=256, rows_per_item=1)
         cfg.update(bad)
         with pytest.raises(P.IsingError):
@@ -170,15 +171,21 @@ def test_tiny_cluster_bit_exact(P, orc, L, ctas, tpw):
     lat.close()
 
 
-def test_warp_specialised_L64_is_bit_exact(P, orc):
-    """L = 64 with 1024 threads and one thread per word runs the warp-specialised
-    kernel (producer warps draw the masks into a ring, consumer warps update):
-    lattice and every sample against the oracle, for several call splits and
-    sample spacings, both parities of the start sweep and record_every = 0."""
-    L, T, seed, sid = 64, 2.269185, 17, 5
+WS_SHAPES = [(64, 1), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4), (128, 8)]
+
+
+@pytest.mark.parametrize("L,ctas", WS_SHAPES)
+def test_warp_specialised_is_bit_exact(P, orc, L, ctas):
+    """1024 threads and one thread per word run the warp-specialised kernel
+    (producer warps draw the masks into a ring, consumer warps update; with a
+    cluster the producers sit in the other CTAs and store into the first CTA's
+    ring through distributed shared memory): lattice and every sample against
+    the oracle, for several call splits and sample spacings, both parities of
+    the start sweep and record_every = 0."""
+    T, seed, sid = 2.269185, 17, 5
     thr4, thr8 = orc.thresholds(T)
     lat = P.Lattice(L, T, seed=seed, stream_id=sid, init="hot")
-    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=1, persistent=0)
+    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=ctas, persistent=0)
     s = orc.init_hot(L, seed, sid)
     t = 0
     for n, rec in ((1, 1), (7, 3), (300, 1), (129, 64), (5, 0), (1000, 7)):
@@ -193,13 +200,14 @@ def test_warp_specialised_L64_is_bit_exact(P, orc):
     lat.close()
 
 
-def test_warp_specialised_wait_runs_out_and_reports(P, monkeypatch):
-    """A step whose masks are never announced: the consumers' bounded wait runs
-    out, the call reports ISING_ERR_TIMEOUT, the handle is failed, and the GPU
-    stays usable."""
-    lat = P.Lattice(64, 2.0, seed=1, init="hot")
-    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=1, persistent=0)
-    monkeypatch.setenv("ISING_TINY_HOLD_STEP", "6")
+@pytest.mark.parametrize("L,ctas,hold", [(64, 1, 6), (64, 4, 6), (128, 8, 6), (64, 1, 20), (64, 4, 20), (128, 8, 20)])
+def test_warp_specialised_wait_runs_out_and_reports(P, monkeypatch, L, ctas, hold):
+    """A step whose masks are never announced (a middle step, or the last of
+    the call's 20): the consumers' bounded wait runs out, the call reports
+    ISING_ERR_TIMEOUT, the handle is failed, and the GPU stays usable."""
+    lat = P.Lattice(L, 2.0, seed=1, init="hot")
+    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=ctas, persistent=0)
+    monkeypatch.setenv("ISING_TINY_HOLD_STEP", str(hold))
     with pytest.raises(P.IsingError) as ei:
         lat.sweep(10, 1, collect=True)
     assert ei.value.status == P.ERR_TIMEOUT
@@ -208,18 +216,19 @@ def test_warp_specialised_wait_runs_out_and_reports(P, monkeypatch):
         lat.sweep(1, 1)
     assert ei.value.status == P.ERR_STATE
     lat.close()
-    ok = P.Lattice(64, 2.0, seed=1, init="hot")
+    ok = P.Lattice(L, 2.0, seed=1, init="hot")
     ok.sweep(10, 1)
     assert ok.measure()["sweeps_done"] == 10
     ok.close()
 
 
-def test_warp_specialised_configuration_in_a_field_runs_the_field_kernel(P, orc):
+@pytest.mark.parametrize("L,ctas", [(64, 1), (128, 4)])
+def test_warp_specialised_configuration_in_a_field_runs_the_field_kernel(P, orc, L, ctas):
     """The warp-specialised configuration has no field form: in a field the
-    one-CTA field kernel runs instead, bit-exact with the oracle."""
-    L, T, H, seed = 64, 2.1, 0.3, 9
+    one-CTA or cluster field kernel runs instead, bit-exact with the oracle."""
+    T, H, seed = 2.1, 0.3, 9
     lat = P.Lattice(L, T, seed=seed, init="hot", H=H)
-    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=1, persistent=0)
+    lat.set_launch(proc_bits=8, regcap=0, insert=0, block=1024, rows_per_item=1, grid=ctas, persistent=0)
     M, E = lat.sweep(12, 1, collect=True)
     s = orc.init_hot(L, seed, 0)
     Mo, Eo = orc.run_field(s, 12, seed, 0, T, H)
