@@ -575,26 +575,40 @@ def run_ours(args, ws, rank, local):
         Mh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
         Eh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
 
+        phases = []
+
         def e2e_step():
+            # each phase ends in a blocking call: ising_create reads the initial
+            # counts back, ising_sweep the samples
+            t0 = time.perf_counter()
             lt = P.Lattice(L, T, seed=SEED, stream_id=rank, packed=hp, word_bits=WORD_BITS, stream=stream)
+            t1 = time.perf_counter()
             P.ising_sweep(lt.handle, SWEEPS_PER_STEP, 1, Mh, Eh, SWEEPS_PER_STEP)
+            t2 = time.perf_counter()
             lt.close()
+            phases.append((t1 - t0, t2 - t1, time.perf_counter() - t2))
 
         # the library's device memory from PyTorch's caching allocator, as a
         # caller that runs job after job would set it up: the 32 GiB lattice is
         # allocated once, not cudaMalloc'd and freed in every step
         P.use_torch_allocator()
+        e2e_clocks = ClockSampler(local)
         try:
             e2e_step()
             barrier()
+            e2e_clocks.start()
+            del phases[:]
             t0 = time.perf_counter()
             for _ in range(args.steps):
                 e2e_step()
             torch.cuda.synchronize()
             t_e2e = max_over_ranks(time.perf_counter() - t0)
+            e2e_clk = e2e_clocks.stop()
         finally:
             P.ising_set_allocator(None)
             torch.cuda.empty_cache()
+        e2e_phases = {k: round(float(np.median([ph[j] for ph in phases])), 4)
+                      for j, k in enumerate(("create_upload_s", "sweeps_s", "close_s"))}
         e2e_value = units_per_step * args.steps / t_e2e / 1e9
         h2d, d2h = nbytes, int(Mh.nbytes + Eh.nbytes)
         del host
@@ -657,7 +671,8 @@ def run_ours(args, ws, rank, local):
         "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                  "how": "per step: ising_create from the pinned packed cold start (H2D), ising_sweep of 10 "
                         "sweeps returning the 10 M/E samples (D2H), ising_destroy; device memory from PyTorch's "
-                        "caching allocator (ising_set_allocator)"}
+                        "caching allocator (ising_set_allocator)",
+                 "phases_median": e2e_phases, "clocks": e2e_clk}
                 if e2e_value is not None else None),
         "gpu_launches": launches,
         "launch": dict(tuned, autotune_us_per_step=tuned_us) if tuned else None,

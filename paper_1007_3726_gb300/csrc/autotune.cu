@@ -44,10 +44,9 @@ LaunchConfig default_launch(int device, uint64_t L, uint32_t word_bits)
     // untuned: the shapes the autotuner picked on GB300 at these sizes
     // (fields: proc_bits, regcap, insert, block, rows_per_item, grid)
     // every sweep of a call in one launch: the warp-specialised cluster kernel
-    // (L = 64: 4 CTAs, L = 128: 8 CTAs), a cluster of 8 CTAs (L = 256, 512)
+    // (L = 64: 4 CTAs, L = 128 and 256: 8 CTAs), a cluster of 8 CTAs (L = 512)
     if (L == 64) return LaunchConfig{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 4};
-    if (L == 128) return LaunchConfig{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 8};
-    if (L == 256) return LaunchConfig{kTinyProcBits, 0, 0, 256, 1, 8};
+    if (L == 128 || L == 256) return LaunchConfig{kTinyProcBits, 0, 0, kTinyWsBlock, 1, 8};
     if (L == 512) return LaunchConfig{kTinyProcBits, 0, 0, 512, 1, 8};
     if (L < 4096) return LaunchConfig{32, 1, 0, 256, 2, 0};
     if (L < 16384) return LaunchConfig{64, 0, 0, 512, 4, 0};

@@ -255,47 +255,52 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Warp-specialised kernels for L = 64 and L = 128 (a row is 2 or 4 words of
+// Warp-specialised kernels for L = 64, 128 and 256 (a row is 2, 4 or 8 words of
 // 32 bits).  A lattice this small leaves most of an SM's issue slots idle when
 // every thread both draws and updates: the dependent bit logic and the
 // barrier of each step are short, the Philox draws long.  The draws do not
 // depend on the spins, so the roles are split:
-//   consumers  one thread per 32-bit word (L * L / 32 threads in the first
-//              CTA).  The lattice stays in registers: the left and right
-//              neighbour words and the rows above and below come from other
-//              lanes by warp shuffles, the rows across a warp boundary through
-//              a small shared-memory array.  A step is the ring entry, the bit
-//              logic, one store of the word's boundary row (lanes off a warp
-//              boundary store to a scratch slot) and one barrier of the
-//              consumers; on a counted sweep the second step also stores the
-//              new word, tagged, into a snapshot ring.  The step has no branch
-//              but one that is taken only when something has to wait (the
-//              ring entry is not there yet, a snapshot slot is still being
-//              read) or a failure is to be acted on.
+//   consumers  threads of the first CTA that keep the lattice in registers:
+//              one word each, or at L = 256 a vertical run of four words of
+//              one column.  The left and right neighbour words come from other
+//              lanes by warp shuffles, so do the rows above and below a run,
+//              and the rows across a warp boundary through a small shared
+//              array.  A step is the ring entries, the bit logic, one store of
+//              the thread's boundary row (a scratch slot off a warp boundary)
+//              and one barrier of the consumers.  The step has no branch but
+//              one that is taken only when something has to wait (a ring entry
+//              is not there yet, a count slot is still being read) or a failure
+//              is to be acted on.
 //   arriver    one thread next to the consumers: it follows their progress
 //              (thread 0 of the consumers publishes each finished step) and
 //              frees each step's ring slot with one arrival on the slot's
-//              mbarrier;
-//   counters   a few warps; counter k takes every few counted sweeps starting
-//              with the k-th: once all tags of the sweep's snapshot are there
-//              it takes M and E of the whole lattice from it, writes the
-//              sample and frees the snapshot slot.  No remote arrival, global
-//              store or count is then on the consumers' path.
-//   producers  groups of L * L / 32 threads; a group draws the masks of every
-//              NG-th step (NG groups in all) and writes them, tagged with the
-//              step, into the group's slot of the consumers' ring: one 64-bit
-//              entry (step + 1) << 32 | masks per word.  It draws the masks of
-//              its next step first and then waits until the slot's previous
-//              entry has been freed, so the draws overlap the wait.
+//              mbarrier; nothing else, so that the producers' slots are freed
+//              as soon as they can be;
+//   counting   on a counted sweep, L = 64 and 128: the consumers' second step
+//              stores the new words, tagged, into a snapshot ring, and a few
+//              counter warps (counter k takes every few counted sweeps starting
+//              with the k-th) take M and E of the whole lattice from a snapshot
+//              once all its tags are there, write the sample and free the slot;
+//              at L = 256, where the producers set the pace and the consumers
+//              have time to spare, each consumer warp counts its own words and
+//              stores one tagged partial count, and a writer warp adds the
+//              warps' partials up and writes the sample.  No remote arrival,
+//              global store or release is then on the consumers' path.
+//   producers  groups of threads (L * L / 32 words; a thread draws two words at
+//              L = 256); a group draws the masks of every NG-th step (NG groups
+//              in all) and writes them, tagged with the step, into the group's
+//              slot of the consumers' ring: one 64-bit entry (step + 1) << 32 |
+//              masks per word.  It draws the masks of its next step first and
+//              then waits until the slot's previous entry has been freed, so
+//              the draws overlap the wait.
 // Two forms:
 //   CL = false  one CTA of 1024 threads for L = 64: 128 consumer threads, the
 //               arriving thread, two counter warps and six producer groups;
 //   CL = true   a thread-block cluster of C CTAs of 1024 threads: CTA 0 holds
-//               the consumers, the arriving thread and four counter warps,
-//               CTAs 1 .. C - 1 the producers (1024 / (L L / 32) groups each),
-//               which store into CTA 0's ring through distributed shared
-//               memory; the arrival goes to the slot's mbarrier in the
-//               producing CTA.  The producers' issue
+//               the consumers, the arriving thread and the counting warps,
+//               CTAs 1 .. C - 1 the producers, which store into CTA 0's ring
+//               through distributed shared memory; the arrival goes to the
+//               slot's mbarrier in the producing CTA.  The producers' issue
 //               slots then no longer compete with the consumers', and C - 1
 //               SMs draw.
 // Ordering.  A consumer's load of a ring entry has returned its value before
@@ -307,12 +312,15 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
 // into a slot can overtake a load of its previous entry; the arrivals and the
 // publication are relaxed (a release at cluster scope would fence every
 // thread's memory operations at every step).  Snapshot entries carry their
-// sweep's tag, and a counter reads one only once the tag is there.
+// sweep's tag (so do the partial counts), and nobody reads one before the
+// tag is there.  A release that frees a snapshot slot or count buffer comes
+// before the sample's global stores, which it would otherwise wait for.
 // Failure.  Every wait is bounded.  A consumer whose wait runs out sets the
 // abort flag of its step's parity before the step's barrier; every consumer
 // reads that flag after the barrier and before the next one, so all of them
-// stop at the same point.  The arriving thread, the counters and the producers stop when their own
-// waits run out; any of them sets *err, so the kernel always ends.  In the
+// stop at the same point.  The arriving thread, the counting warps and the
+// producers stop when their own waits run out; any of them sets *err, so the
+// kernel always ends.  In the
 // cluster form every thread reaches a final cluster barrier, so no CTA leaves
 // while another may still use its shared memory.
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -327,7 +335,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 constexpr uint32_t kWsSpinLimit = 1u << 24;  // polls of a consumer's wait before it gives up
 constexpr uint32_t kWsWaitLimit = 1u << 20;  // polls of a producer's mbarrier wait
 constexpr uint32_t kWsMaxGroups = 7 * (kTinyWsBlock / 128);  // L = 64 on a cluster of 8
-constexpr uint32_t kWsSnaps = 8;             // counted sweeps the consumers may run ahead of the counters
 
 __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank)
 {
@@ -434,44 +441,78 @@ struct WsParity {
     static constexpr uint32_t value = V;
 };
 
+// The shape of the warp-specialised kernel at L = LL.
+template <uint32_t LL, bool CL>
+struct WsShape {
+    static constexpr uint32_t W = LL / 32;                  // words per row
+    static constexpr uint32_t NWORDS = LL * W;              // words of the lattice
+    static constexpr uint32_t WPT = LL >= 256 ? NWORDS / 512 : 1;  // words per consumer thread
+    static constexpr uint32_t NCONS = NWORDS / WPT;         // consumer threads
+    static constexpr uint32_t NCW = NCONS / 32;             // consumer warps
+    static constexpr uint32_t GT = NWORDS < kTinyWsBlock ? NWORDS : kTinyWsBlock;  // threads of a producer group
+    static constexpr uint32_t PW = NWORDS / GT;             // words per producer thread
+    static constexpr uint32_t GPC = kTinyWsBlock / GT;      // producer groups per producer CTA
+    // where the consumers have slack (the producers set the pace: L = 256),
+    // they count on recorded sweeps themselves; else snapshots and counter warps
+    static constexpr bool INLINE = LL >= 256;
+    static constexpr uint32_t NCOUNT = INLINE ? 0 : CL ? 4 : 2;  // counter warps
+    static constexpr uint32_t SNAPS = INLINE ? 0 : 8;       // snapshot slots
+    // CL = false: the producer groups beside the consumers, the arriving
+    // thread's warp and the counter warps, and the threads left over
+    static constexpr uint32_t GLOCAL = (kTinyWsBlock - NCONS - 32 - 32 * NCOUNT) / GT;
+    static constexpr uint32_t IDLE = CL ? 0 : kTinyWsBlock - NCONS - 32 - 32 * NCOUNT - GLOCAL * GT;
+    static_assert(CL || (LL == 64 && GLOCAL >= 1), "the one-CTA form is for L = 64");
+    static_assert(NCONS + 32 + 32 * NCOUNT <= kTinyWsBlock, "the first CTA holds consumers, arriver and counters");
+    __host__ __device__ static uint32_t groups(uint32_t ctas) { return CL ? GPC * (ctas - 1) : GLOCAL; }
+    // dynamic shared memory: the ring (a slot per group) and the snapshot slots
+    static size_t smem(uint32_t ctas) { return (size_t)(groups(ctas) + SNAPS) * NWORDS * 8; }
+};
+
 template <uint32_t LL, bool CL>
 __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant__ TinyRunArgs A)
 {
-    constexpr uint32_t W = LL / 32;              // words per row
-    constexpr uint32_t NWORDS = LL * W;          // consumer threads, threads of a producer group
-    constexpr uint32_t NCW = NWORDS / 32;        // consumer warps
-    constexpr uint32_t GPC = kTinyWsBlock / NWORDS;  // producer groups per producer CTA
-    constexpr uint32_t NCOUNT = CL ? 4 : 2;      // counter warps
-    // CL = false: producer groups beside the consumers, the arriving thread's
-    // warp and the counter warps, and the threads left over
-    constexpr uint32_t GLOCAL = (kTinyWsBlock - NWORDS - 32 - 32 * NCOUNT) / NWORDS;
-    constexpr uint32_t IDLE = CL ? 0 : kTinyWsBlock - NWORDS - 32 - 32 * NCOUNT - GLOCAL * NWORDS;
+    using S = WsShape<LL, CL>;
+    constexpr uint32_t W = S::W, NWORDS = S::NWORDS, WPT = S::WPT, NCONS = S::NCONS, NCW = S::NCW;
+    constexpr uint32_t GT = S::GT, PW = S::PW, GPC = S::GPC, NCOUNT = S::NCOUNT;
+    constexpr uint32_t SNAPS = S::SNAPS;
+    constexpr uint32_t SN = SNAPS ? SNAPS : 1u;  // snapshot slots in index arithmetic (no slot when counting inline)
     constexpr uint32_t kStopped = 0xFFFFFFFFu;
-    constexpr uint32_t NB = 2 * NCW * W;         // boundary rows; then one scratch slot per consumer
-    static_assert(CL || LL == 64, "the one-CTA form is for L = 64");
-    extern __shared__ __align__(16) uint64_t ring[];  // [NG][NWORDS], in CTA 0
+    constexpr uint32_t NB = 2 * NCW * W;  // warps' first and last rows; then one scratch slot per consumer
+    // dynamic: the ring [NG][NWORDS] ((step + 1) << 32 | masks), then the
+    // snapshots [SNAPS][NWORDS] ((sweep tag) << 32 | word) of the lattice after
+    // counted sweeps; both used in CTA 0 only
+    extern __shared__ __align__(16) uint64_t dyn[];
     __shared__ __align__(8) uint64_t empty[kWsMaxGroups];  // per slot: one arrival frees it
-    __shared__ uint32_t bnd[NB + NWORDS];  // first rows of the consumer warps, last rows, scratch
-    // snapshots (sweep tag << 32 | word) of the lattice after counted sweeps, and a scratch row
-    __shared__ __align__(8) uint64_t snap[kWsSnaps + 1][NWORDS];
+    __shared__ uint32_t bnd[NB + NCONS];  // first rows of the consumer warps, last rows, scratch
     // per snapshot slot: how many snapshots the counter warps have read from it
-    __shared__ uint32_t slot_read[kWsSnaps];
+    __shared__ uint32_t slot_read[SN];
+    // inline counting: each consumer warp's counts of the last NCB counted
+    // sweeps (sweep tag << 48 | anti-aligned bonds << 24 | up spins), and how
+    // many counted sweeps the writer warp has read
+    constexpr uint32_t NCB = 8;  // count buffers (counted sweeps the consumers may run ahead of the writer)
+    __shared__ __align__(8) unsigned long long cnt[NCB][NCW];
+    __shared__ uint32_t cnt_done;
     __shared__ uint32_t done_step, abort_flag[2];
     const uint32_t tid = threadIdx.x;
     const uint32_t rank = CL ? cluster_rank() : 0u;
-    const uint32_t NG = CL ? GPC * (gridDim.x - 1) : GLOCAL;
+    const uint32_t NG = S::groups(CL ? gridDim.x : 1u);
+    uint64_t *const ring = dyn;
+    uint64_t *const snap = dyn + (size_t)NG * NWORDS;
     const uint32_t nsteps = 2 * A.nsweeps;
     // a held step (failure testing) runs the waits out quickly
     const uint32_t limit = A.hold_step ? (1u << 14) : kWsSpinLimit;
     const uint32_t plimit = A.hold_step ? (1u << 12) : kWsWaitLimit;
     if (rank == 0) {
         for (uint32_t i = tid; i < NG * NWORDS; i += kTinyWsBlock) ring[i] = 0ull;
-        for (uint32_t i = tid; i < kWsSnaps * NWORDS; i += kTinyWsBlock) (&snap[0][0])[i] = 0ull;
+        if constexpr (SNAPS != 0)
+            for (uint32_t i = tid; i < SNAPS * NWORDS; i += kTinyWsBlock) snap[i] = 0ull;
     }
     if (tid == 0) {
         for (uint32_t k = 0; k < NG; ++k) mbar_init(&empty[k], 1u);
         done_step = 0u;
-        for (uint32_t k = 0; k < kWsSnaps; ++k) slot_read[k] = 0u;
+        for (uint32_t k = 0; k < SN; ++k) slot_read[k] = 0u;
+        for (uint32_t k = 0; k < NCB * NCW; ++k) (&cnt[0][0])[k] = 0ull;
+        cnt_done = 0u;
         abort_flag[0] = 0u;
         abort_flag[1] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -481,51 +522,73 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
     else
         __syncthreads();
 
-    const bool consumer = rank == 0 && tid < NWORDS;
-    const bool arriver = rank == 0 && tid == NWORDS;
-    const bool counter = rank == 0 && tid >= NWORDS + 32 && tid < NWORDS + 32 + 32 * NCOUNT;
-    const bool producer = CL ? rank != 0 : (tid >= NWORDS + 32 + 32 * NCOUNT && tid < kTinyWsBlock - IDLE);
+    const bool consumer = rank == 0 && tid < NCONS;
+    const bool arriver = rank == 0 && tid == NCONS;
+    const bool writer = S::INLINE && rank == 0 && tid >= NCONS + 32 && tid < NCONS + 64;
+    const bool counter = rank == 0 && tid >= NCONS + 32 && tid < NCONS + 32 + 32 * NCOUNT;
+    const bool producer = CL ? rank != 0 : (tid >= NCONS + 32 + 32 * NCOUNT && tid < kTinyWsBlock - S::IDLE);
     if (producer) {
         HalfSweepArgs a;
         a.key = A.key;
         a.thr4 = A.thr4;
         a.thr8 = A.thr8;
         a.zero = 0u;
-        const uint32_t pt = CL ? tid : tid - NWORDS - 32 - 32 * NCOUNT;
-        const uint32_t G = (CL ? (rank - 1) * GPC : 0u) + pt / NWORDS, w = pt % NWORDS;
-        const uint64_t g = (uint64_t)(w / W) * (LL >> 3) + (uint64_t)(w % W) * 4u;
-        const uint32_t dst = CL ? mapa_shared(smem_addr(&ring[G * NWORDS + w]), 0u) : smem_addr(&ring[G * NWORDS + w]);
+        const uint32_t pt = CL ? tid : tid - NCONS - 32 - 32 * NCOUNT;
+        const uint32_t G = (CL ? (rank - 1) * GPC : 0u) + pt / GT, tl = pt % GT;
+        // words tl, tl + GT, ... of the lattice
+        uint64_t g[PW];
+        uint32_t dst[PW];
+#pragma unroll
+        for (uint32_t k = 0; k < PW; ++k) {
+            const uint32_t w = tl + k * GT;
+            g[k] = (uint64_t)(w / W) * (LL >> 3) + (uint64_t)(w % W) * 4u;
+            const uint32_t la = smem_addr(&ring[G * NWORDS + w]);
+            dst[k] = CL ? mapa_shared(la, 0u) : la;
+        }
         const uint32_t slot_bar = smem_addr(&empty[G]);
         for (uint32_t s = G; s < nsteps; s += NG) {
             tiny_step_values(a, A, A.t0 + (s >> 1), s & 1u);
-            uint32_t h4[1], h8[1];
-            word_draw_masks<4, 0, 4>(a, a, g, h4, h8);
+            uint32_t pk[PW];
+#pragma unroll
+            for (uint32_t k = 0; k < PW; ++k) {
+                uint32_t h4[1], h8[1];
+                word_draw_masks<4, 0, 4>(a, a, g[k], h4, h8);
+                pk[k] = pack_masks(h4[0], h8[0]);
+            }
             // the slot's previous entry (step s - NG) must have been freed
             if (s >= NG && !slot_wait<CL>(slot_bar, ((s / NG) & 1u) ^ 1u, plimit)) {
                 if (A.err) atomicExch(A.err, 1u);
                 break;
             }
             if (A.hold_step == s + 1) continue;  // never published (failure testing)
-            ring_store<CL>(dst, ((uint64_t)(s + 1) << 32) | pack_masks(h4[0], h8[0]));
+#pragma unroll
+            for (uint32_t k = 0; k < PW; ++k) ring_store<CL>(dst[k], ((uint64_t)(s + 1) << 32) | pk[k]);
         }
     } else if (consumer) {
-        // thread c holds word c: row c / W, word c % W
-        const uint32_t c = tid, q = c >> 5, l = c & 31u, w = c % W;
-        const uint32_t row_off = (c / W) & 1u;  // parity of the row
+        // thread c holds a vertical run of WPT words: column w = c % W of rows
+        // r WPT .. r WPT + WPT - 1 (r = c / W); the rows above and below the
+        // inner words are the thread's own, a run's first and last rows come
+        // from the lanes W before and after, and a warp's first and last rows
+        // through the boundary array
+        const uint32_t c = tid, q = c >> 5, l = c & 31u, w = c % W, r = c / W;
+        const uint32_t j0 = r * WPT * W + w;  // word index of the run's first word (then + k W)
         const uint32_t lane_l = (l & ~(W - 1u)) | ((w + W - 1u) & (W - 1u));
         const uint32_t lane_r = (l & ~(W - 1u)) | ((w + 1u) & (W - 1u));
-        const uint32_t qu = (q + NCW - 1u) % NCW, qd = (q + 1u) % NCW;
         const bool top = l < W, bottom = l >= 32u - W;
-        // this word's boundary slot (first row, last row or scratch), and the
-        // slots of the row above a warp's first row and below its last row
+        // this thread's boundary slot (its warp's first row, last row, or a
+        // scratch slot), and the slots of the rows above and below the warp
         const uint32_t my_b = top ? q * W + w : bottom ? NCW * W + q * W + w : NB + c;
-        const uint32_t up_b = NCW * W + qu * W + w, dn_b = qd * W + w;
-        uint32_t v = static_cast<const uint32_t *>(A.spins)[c];
-        bnd[my_b] = v;
-        asm volatile("bar.sync 1, %0;" ::"r"(NWORDS) : "memory");  // the initial boundary rows
-        const uint32_t ring0 = smem_addr(&ring[c]);
+        const uint32_t up_b = NCW * W + ((q + NCW - 1u) % NCW) * W + w, dn_b = ((q + 1u) % NCW) * W + w;
+        uint32_t v[WPT];
+#pragma unroll
+        for (uint32_t k = 0; k < WPT; ++k) v[k] = static_cast<const uint32_t *>(A.spins)[j0 + k * W];
+        bnd[my_b] = top ? v[0] : v[WPT - 1];
+        asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");  // the initial boundary rows
+        const uint32_t ring0 = smem_addr(&ring[j0]);
+        const uint32_t snap0 = smem_addr(&snap[j0]);
         const uint32_t abort0 = smem_addr(&abort_flag[0]);
         const uint32_t sread0 = smem_addr(&slot_read[0]);
+        const uint32_t cnt_done0 = smem_addr(&cnt_done);
         const uint32_t done_addr = smem_addr(&done_step);
         uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;
         uint32_t G = 0, s = 0, cidx = 0, sread = 0;
@@ -535,50 +598,115 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
         auto step = [&](auto pc, bool counted) -> bool {
             constexpr uint32_t p = decltype(pc)::value;
             const uint32_t ea = ring0 + G * (NWORDS * 8u);
-            uint64_t e = ring_load<CL>(ea);
-            const uint32_t vl = __shfl_sync(0xFFFFFFFFu, v, lane_l);
-            const uint32_t vr = W == 2 ? vl : __shfl_sync(0xFFFFFFFFu, v, lane_r);
-            const uint32_t su = __shfl_up_sync(0xFFFFFFFFu, v, W);
-            const uint32_t sd = __shfl_down_sync(0xFFFFFFFFu, v, W);
+            uint64_t e[WPT];
+#pragma unroll
+            for (uint32_t k = 0; k < WPT; ++k) e[k] = ring_load<CL>(ea + k * (W * 8u));
+            uint32_t vl[WPT], vr[WPT];
+#pragma unroll
+            for (uint32_t k = 0; k < WPT; ++k) {
+                vl[k] = __shfl_sync(0xFFFFFFFFu, v[k], lane_l);
+                vr[k] = W == 2 ? vl[k] : __shfl_sync(0xFFFFFFFFu, v[k], lane_r);
+            }
+            const uint32_t su = __shfl_up_sync(0xFFFFFFFFu, v[WPT - 1], W);
+            const uint32_t sd = __shfl_down_sync(0xFFFFFFFFu, v[0], W);
             const uint32_t bu = bnd[up_b], bd = bnd[dn_b];
+            const uint32_t vu0 = top ? bu : su;          // the row above the run
+            const uint32_t vdl = bottom ? bd : sd;       // the row below the run
             // set (before the previous barrier) by a consumer whose wait ran out
             const uint32_t ab = ld_volatile_u32(abort0 + 4u * (p ^ 1u));
             const uint32_t tag = s + 1u;
-            const uint32_t sslot = cidx % kWsSnaps, sneed = cidx / kWsSnaps;
+            const uint32_t sslot = cidx % SN, sneed = cidx / SN;
             // the snapshot slot of this sweep: read by the counters as often as
             // it has been written (loaded at the sweep's first step, checked at
             // its second, where the snapshot is stored)
-            if constexpr (p == 0u) sread = ld_volatile_u32(sread0 + 4u * sslot);
-            const bool snap_wait = p == 1u && counted && sread < sneed;
-            if (((uint32_t)(e >> 32) != tag) | (ab != 0u) | snap_wait) {
+            bool snap_wait = false;
+            if constexpr (S::INLINE) {
+                // lane 0 of each warp stores into cnt[cidx % NCB], which the
+                // writer must have read for counted sweep cidx - NCB
+                if constexpr (p == 0u) sread = l == 0 ? ld_volatile_u32(cnt_done0) : 0u;
+                snap_wait = p == 1u && counted && l == 0 && sread + NCB <= cidx;
+            } else {
+                if constexpr (p == 0u) sread = ld_volatile_u32(sread0 + 4u * sslot);
+                snap_wait = p == 1u && counted && sread < sneed;
+            }
+            bool have = true;
+#pragma unroll
+            for (uint32_t k = 0; k < WPT; ++k) have &= (uint32_t)(e[k] >> 32) == tag;
+            if (!have | (ab != 0u) | snap_wait) {
                 if (ab != 0u) return false;  // every consumer has read the same flag
                 bool fail = false;
-                for (uint32_t n = 0; (uint32_t)(e >> 32) != tag; ++n) {
+                for (uint32_t n = 0; !have; ++n) {
                     if (n >= limit) {
                         fail = true;
                         break;
                     }
-                    e = ring_load<CL>(ea);
+                    have = true;
+#pragma unroll
+                    for (uint32_t k = 0; k < WPT; ++k) {
+                        e[k] = ring_load<CL>(ea + k * (W * 8u));
+                        have &= (uint32_t)(e[k] >> 32) == tag;
+                    }
                 }
-                // the snapshot slot's previous snapshot must have been read
-                for (uint32_t m = 0; snap_wait && sread < sneed; ++m) {
+                // the snapshot slot's previous snapshot must have been read (or
+                // the count buffer written out)
+                for (uint32_t m = 0; snap_wait && (S::INLINE ? sread + NCB <= cidx : sread < sneed); ++m) {
                     if (m >= limit) {
                         fail = true;
                         break;
                     }
-                    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(sread) : "r"(sread0 + 4u * sslot) : "memory");
+                    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];"
+                                 : "=r"(sread)
+                                 : "r"(S::INLINE ? cnt_done0 : sread0 + 4u * sslot)
+                                 : "memory");
                 }
                 if (fail) abort_flag[p] = 1u;
             }
-            const uint32_t vu = top ? bu : su, vd = bottom ? bd : sd;
-            v = ws_update_word(v, vu, vd, vl, vr, row_off ^ p, (uint32_t)e);
-            bnd[my_b] = v;
-            if constexpr (p == 1u) {
-                // counted sweep: the snapshot slot; otherwise the scratch row
-                const uint32_t k = counted ? sslot : kWsSnaps;
-                snap[k][c] = ((uint64_t)(cidx + 1u) << 32) | v;
+            // word k of the run: row r WPT + k; its rows above and below are
+            // read only at the sites of the other parity, which this step
+            // leaves as they were (so a word already updated may serve)
+#pragma unroll
+            for (uint32_t k = 0; k < WPT; ++k) {
+                const uint32_t up = k == 0 ? vu0 : v[k - 1], dn = k + 1 == WPT ? vdl : v[k + 1];
+                v[k] = ws_update_word(v[k], up, dn, vl[k], vr[k], ((r * WPT + k) & 1u) ^ p, (uint32_t)e[k]);
             }
-            asm volatile("bar.sync 1, %0;" ::"r"(NWORDS) : "memory");
+            bnd[my_b] = top ? v[0] : v[WPT - 1];
+            if constexpr (S::INLINE && p == 1u) {
+                if (counted) {  // uniform: the sweep is counted or not for every consumer
+                    // up spins, and the anti-aligned bonds of the updated sites
+                    // (every bond once on the second step); two bond masks of
+                    // one parity share a word once one is rotated by one bit
+                    // (the neighbours at the updated sites are of the other
+                    // parity, the same before and after the step)
+                    uint32_t cu = 0, ca = 0;
+#pragma unroll
+                    for (uint32_t k = 0; k < WPT; ++k) {
+                        const uint32_t sel = 0x55555555u << (((r * WPT + k) & 1u) ^ 1u);
+                        const uint32_t nu = k == 0 ? vu0 : v[k - 1], nd = k + 1 == WPT ? vdl : v[k + 1];
+                        const uint32_t left = __funnelshift_l(vl[k], v[k], 1), right = __funnelshift_r(v[k], vr[k], 1);
+                        const uint32_t b1 = sel & (v[k] ^ nu), b2 = sel & (v[k] ^ nd);
+                        const uint32_t b3 = sel & (v[k] ^ left), b4 = sel & (v[k] ^ right);
+                        cu += __popc(v[k]);
+                        ca += __popc(b1 | __funnelshift_l(b2, b2, 1)) + __popc(b3 | __funnelshift_l(b4, b4, 1));
+                    }
+                    // this warp's counts (up spins <= 4096, bonds <= 8192) with the
+                    // sweep's tag, into the warp's own slot: one store, no atomic
+                    const unsigned long long part = (unsigned long long)__reduce_add_sync(0xFFFFFFFFu, cu) |
+                                                    ((unsigned long long)__reduce_add_sync(0xFFFFFFFFu, ca) << 24) |
+                                                    ((unsigned long long)((cidx + 1u) & 0xFFFFu) << 48);
+                    if (l == 0) *(volatile unsigned long long *)&cnt[cidx % NCB][q] = part;
+                }
+            }
+            if constexpr (!S::INLINE && p == 1u) {
+                // a counted sweep: the tagged words into the snapshot slot
+                const uint32_t sa = snap0 + sslot * (NWORDS * 8u);
+#pragma unroll
+                for (uint32_t k = 0; k < WPT; ++k)
+                    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.volatile.shared.u64 [%1], %2;\n\t}" ::"r"(
+                                     (uint32_t)counted),
+                                 "r"(sa + k * (W * 8u)), "l"(((uint64_t)(cidx + 1u) << 32) | v[k])
+                                 : "memory");
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(NCONS) : "memory");
             // every consumer is done with step s: thread 0 publishes it
             asm volatile("{\n\t.reg .pred q;\n\tsetp.eq.u32 q, %0, 0;\n\t@q st.volatile.shared.u32 [%1], %2;\n\t}" ::"r"(c),
                          "r"(done_addr), "r"(tag)
@@ -593,7 +721,19 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
             return counted;
         };
         uint32_t i = 0;
-        for (; i + 2 <= A.nsweeps; i += 2) {
+        // two sweeps per iteration where a thread holds one word; with several
+        // words a step's code is long, and one sweep per iteration keeps the
+        // loop within the instruction cache
+        constexpr uint32_t SW = WPT == 1 ? 2u : 1u;
+        for (; SW == 1 && i < A.nsweeps; ++i) {
+            const bool c0 = sweep_counted() || i + 1 == A.nsweeps;
+            if (!step(WsParity<0>{}, c0) || !step(WsParity<1>{}, c0)) {
+                stop = true;
+                break;
+            }
+            if (c0) ++cidx;
+        }
+        for (; SW == 2 && i + 2 <= A.nsweeps; i += 2) {
             const bool c0 = sweep_counted() || i + 1 == A.nsweeps;
             const bool c1 = sweep_counted() || i + 2 == A.nsweeps;
             if (!step(WsParity<0>{}, c0) || !step(WsParity<1>{}, c0)) {
@@ -607,10 +747,9 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
             }
             if (c1) ++cidx;
         }
-        if (!stop && i < A.nsweeps) {  // an odd number of sweeps: the last one
-            const bool c0 = true;      // the last sweep is always counted
+        if (!stop && i < A.nsweeps) {  // an odd number of sweeps: the last one (always counted)
             (void)sweep_counted();
-            if (!step(WsParity<0>{}, c0) || !step(WsParity<1>{}, c0))
+            if (!step(WsParity<0>{}, true) || !step(WsParity<1>{}, true))
                 stop = true;
             else
                 ++cidx;
@@ -624,7 +763,8 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
                 if (A.err) atomicExch(A.err, 1u);
             }
         } else {
-            static_cast<uint32_t *>(A.spins)[c] = v;
+#pragma unroll
+            for (uint32_t k = 0; k < WPT; ++k) static_cast<uint32_t *>(A.spins)[j0 + k * W] = v[k];
         }
     } else if (arriver) {
         // frees each finished step's ring slot: one arrival on the slot's
@@ -648,6 +788,72 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
                 G = G + 1u == NG ? 0u : G + 1u;
             } while (++next < d);
         }
+    } else if (writer) {
+        // inline counting: after the second step of each counted sweep, the
+        // consumer warps' counts, once all carry the sweep's tag (they were
+        // stored before the barrier of that step), go out as the sample.  A
+        // warp of its own (lane k reads warp k's slot, so the reads are one
+        // round trip however busy shared memory is), so that its global
+        // stores and release never delay the arrivals that free the
+        // producers' slots.
+        static_assert(NCW <= 32, "one slot per lane");
+        const uint32_t hl = tid & 31u;
+        const uint32_t done_addr = smem_addr(&done_step);
+        uint32_t next = 0, n = 0, slot = 0, ccount = 0;
+        uint32_t phase = A.record_every ? A.t0 % A.record_every : 0u;
+        bool quit = false;
+        while (next < nsteps && !quit) {
+            uint32_t d = hl == 0 ? ld_volatile_u32(done_addr) : 0u;
+            d = __shfl_sync(0xFFFFFFFFu, d, 0);
+            if (d == kStopped) break;
+            if (d <= next) {
+                if (++n >= 4 * limit) {  // longer than a consumer's wait: the consumers report first
+                    if (A.err && hl == 0) atomicExch(A.err, 1u);
+                    break;
+                }
+                continue;
+            }
+            n = 0;
+            do {
+                const uint32_t p = next & 1u;
+                const bool rec = A.record_every != 0u && phase + 1 == A.record_every;
+                const bool last = next + 1 == nsteps;
+                if (p == 1u) {
+                    if (rec || last) {
+                        const unsigned long long want = (unsigned long long)((ccount + 1u) & 0xFFFFu) << 48;
+                        const uint32_t a = smem_addr(&cnt[ccount % NCB][hl < NCW ? hl : 0u]);
+                        unsigned long long part = hl < NCW ? ld_volatile_u64(a) : want;
+                        for (uint32_t m = 0; (part & (0xFFFFull << 48)) != want && m < limit; ++m) part = ld_volatile_u64(a);
+                        if (!__all_sync(0xFFFFFFFFu, (part & (0xFFFFull << 48)) == want)) {
+                            if (A.err && hl == 0) atomicExch(A.err, 1u);
+                            quit = true;
+                            break;
+                        }
+                        const uint32_t c0 = __reduce_add_sync(0xFFFFFFFFu, hl < NCW ? (uint32_t)(part & 0xFFFFFFull) : 0u);
+                        const uint32_t c1 =
+                            __reduce_add_sync(0xFFFFFFFFu, hl < NCW ? (uint32_t)((part >> 24) & 0xFFFFFFull) : 0u);
+                        ++ccount;
+                        __syncwarp();  // every lane has read its slot
+                        if (hl == 0) {
+                            // the buffer is free again (released before the global
+                            // stores below, which a release would otherwise wait for)
+                            asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_addr(&cnt_done)), "r"(ccount)
+                                         : "memory");
+                            if (rec) {
+                                A.acc[2 * slot] = c0;
+                                A.acc[2 * slot + 1] = c1;
+                            }
+                            if (last) {
+                                A.acc[2 * A.nrec] = c0;
+                                A.acc[2 * A.nrec + 1] = c1;
+                            }
+                        }
+                    }
+                    if (rec) ++slot;
+                    if (A.record_every) phase = (phase + 1 == A.record_every) ? 0u : phase + 1;
+                }
+            } while (++next < d);
+        }
     } else if (counter) {
         // counter warp k takes the counted sweeps k, k + NCOUNT, ...: M and E
         // of the whole lattice from the sweep's snapshot, once all its tags
@@ -655,7 +861,7 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
         // the right is in the same row of the same lane group, the word below
         // W lanes on (or, for the last rows of a group, in the next group).
         constexpr uint32_t R = NWORDS / 32;
-        const uint32_t k = (tid - NWORDS - 32) >> 5, hl = tid & 31u;
+        const uint32_t k = (tid - NCONS - 32) >> 5, hl = tid & 31u;
         const uint32_t re = A.record_every;
         const uint32_t first = re ? (re - (A.t0 % re + 1u) % re) % re : 0u;  // first recorded sweep
         const bool last_rec = re != 0u && A.nrec != 0u && first + (A.nrec - 1u) * re + 1u == A.nsweeps;
@@ -664,18 +870,14 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
         const uint32_t lane_d = (hl + W) & 31u;
         const uint32_t done_addr = smem_addr(&done_step);
         for (uint32_t cidx = k; cidx < ncounted; cidx += NCOUNT) {
-            const uint32_t ks = cidx % kWsSnaps, want = cidx + 1u;
-            uint32_t x[R];
+            const uint32_t ks = cidx % SN, want = cidx + 1u;
+            const uint32_t sbase = smem_addr(&snap[(size_t)ks * NWORDS + hl]);
             uint32_t n = 0, seen = 0;
             bool ok = false, quit = false;
             for (;;) {
                 bool all = true;
-#pragma unroll
-                for (uint32_t m = 0; m < R; ++m) {
-                    const uint64_t e = ld_volatile_u64(smem_addr(&snap[ks][hl + 32u * m]));
-                    x[m] = (uint32_t)e;
-                    all &= (uint32_t)(e >> 32) == want;
-                }
+#pragma unroll 4
+                for (uint32_t m = 0; m < R; ++m) all &= (uint32_t)(ld_volatile_u64(sbase + m * 256u) >> 32) == want;
                 if (__all_sync(0xFFFFFFFFu, all)) {
                     ok = true;
                     break;
@@ -698,19 +900,33 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
                 if (A.err && hl == 0) atomicExch(A.err, 1u);
                 break;
             }
-            uint32_t part = 0;  // packed: up spins <= 16384, anti-aligned bonds <= 32768
-#pragma unroll
+            __syncwarp();  // every tag seen before any lane reads the words
+            uint32_t part = 0;  // packed: up spins <= 65536 / 2, anti-aligned bonds <= 2 L^2
+            uint32_t up = 0;
+            uint32_t cur = (uint32_t)ld_volatile_u64(sbase);
+#pragma unroll 4
             for (uint32_t m = 0; m < R; ++m) {
-                const uint32_t xr = __shfl_sync(0xFFFFFFFFu, x[m], lane_r);  // the word to the right
-                const uint32_t dn_same = __shfl_sync(0xFFFFFFFFu, x[m], lane_d);
-                const uint32_t dn_next = __shfl_sync(0xFFFFFFFFu, x[(m + 1u) % R], lane_d);
+                const uint32_t nxt = (uint32_t)ld_volatile_u64(sbase + ((m + 1u) % R) * 256u);
+                const uint32_t xr = __shfl_sync(0xFFFFFFFFu, cur, lane_r);  // the word to the right
+                const uint32_t dn_same = __shfl_sync(0xFFFFFFFFu, cur, lane_d);
+                const uint32_t dn_next = __shfl_sync(0xFFFFFFFFu, nxt, lane_d);
                 const uint32_t xd = hl + W < 32u ? dn_same : dn_next;  // the word below
-                const uint32_t right = __funnelshift_r(x[m], xr, 1);    // site x + 1
-                part += __popc(x[m]) + ((uint32_t)(__popc(x[m] ^ right) + __popc(x[m] ^ xd)) << 16);
+                const uint32_t right = __funnelshift_r(cur, xr, 1);    // site x + 1
+                up += __popc(cur);
+                part += __popc(cur ^ right) + __popc(cur ^ xd);
+                cur = nxt;
             }
-            const uint32_t sum = __reduce_add_sync(0xFFFFFFFFu, part);
+            const uint32_t sum_up = __reduce_add_sync(0xFFFFFFFFu, up);
+            const uint32_t sum_anti = __reduce_add_sync(0xFFFFFFFFu, part);
+            __syncwarp();  // every lane has read the snapshot
+            // the slot is free again (released before the global stores below,
+            // which a release would otherwise wait for)
+            if (hl == 0)
+                asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_addr(&slot_read[ks])),
+                             "r"(cidx / SN + 1u)
+                             : "memory");
             if (hl == 0) {
-                const unsigned long long c0 = sum & 0xFFFFu, c1 = sum >> 16;
+                const unsigned long long c0 = sum_up, c1 = sum_anti;
                 const bool rec = cidx < A.nrec;
                 const bool last = !rec || first + cidx * re + 1u == A.nsweeps;
                 if (rec) {
@@ -722,11 +938,6 @@ __global__ void __launch_bounds__(kTinyWsBlock) k_tiny_wsc(const __grid_constant
                     A.acc[2 * A.nrec + 1] = c1;
                 }
             }
-            __syncwarp();  // every lane has read the snapshot
-            if (hl == 0)
-                asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_addr(&slot_read[ks])),
-                             "r"(cidx / kWsSnaps + 1u)
-                             : "memory");
         }
     }
     if constexpr (CL) cluster_barrier();  // no CTA leaves while another may still use its shared memory
@@ -944,7 +1155,7 @@ bool tiny_lattice_ok(uint64_t L) { return L >= 64 && L <= 1024 && (L & (L - 1)) 
 
 bool tiny_config_valid(const LaunchConfig &c, uint64_t L, uint64_t rows)
 {
-    if (c.proc_bits == kTinyProcBits && (L == 64 || L == 128) && rows == L && c.block == kTinyWsBlock &&
+    if (c.proc_bits == kTinyProcBits && (L == 64 || L == 128 || L == 256) && rows == L && c.block == kTinyWsBlock &&
         c.rows_per_item == 1 && c.regcap == 0 && c.insert == 0 && c.persistent == 0)
         // the warp-specialised kernels: one CTA (L = 64) or a cluster of 2, 4 or 8
         return (c.grid == 1 && L == 64) || c.grid == 2 || c.grid == 4 || c.grid == 8;
@@ -964,48 +1175,54 @@ LaunchConfig plain_launch(const LaunchConfig &c)
     return LaunchConfig{32, 1, 0, 256, 2, 0};  // the step shape of small lattices
 }
 
-// The warp-specialised kernels (L = 64 or 128): one CTA for L = 64, else a
-// cluster of `ctas` CTAs whose first CTA holds the consumers.
+// The warp-specialised kernels (L = 64, 128 or 256): one CTA for L = 64, else
+// a cluster of `ctas` CTAs whose first CTA holds the consumers.
+template <uint32_t LL, bool CL>
+static cudaError_t launch_wsc(const TinyRunArgs &a, uint32_t ctas, cudaStream_t s)
+{
+    using Shape = WsShape<LL, CL>;
+    const size_t smem = Shape::smem(ctas);
+    // the dynamic ring and snapshots (up to 176 KB at L = 256) with the static
+    // arrays pass the 48 KB that need no opt-in
+    cudaError_t e = cudaFuncSetAttribute(k_tiny_wsc<LL, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if constexpr (!CL) {
+        k_tiny_wsc<LL, CL><<<1, kTinyWsBlock, smem, s>>>(a);
+        return cudaGetLastError();
+    } else {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(ctas);
+        cfg.blockDim = dim3(kTinyWsBlock);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr{};
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = ctas;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_tiny_wsc<LL, CL>, a);
+    }
+}
+
 static cudaError_t launch_tiny_ws(const TinyRunArgs &a, uint32_t ctas, cudaStream_t s)
 {
-    const uint32_t nwords = (uint32_t)(a.L * a.L / 32);
-    const uint32_t gpc = kTinyWsBlock / nwords;
-    if (ctas == 1) {
-        if (a.L != 64) return cudaErrorInvalidValue;
-        // the producer groups beside the consumers, the arriving thread's warp
-        // and the two counter warps
-        const size_t smem = (size_t)((kTinyWsBlock - nwords - 32 - 64) / nwords) * nwords * 8;
-        k_tiny_wsc<64, false><<<1, kTinyWsBlock, smem, s>>>(a);
-        return cudaGetLastError();
-    }
+    if (ctas == 1) return a.L == 64 ? launch_wsc<64, false>(a, 1, s) : cudaErrorInvalidValue;
     if (ctas != 2 && ctas != 4 && ctas != 8) return cudaErrorInvalidValue;
-    using TinyKernel = void (*)(TinyRunArgs);
-    const TinyKernel kern = a.L == 64 ? k_tiny_wsc<64, true> : k_tiny_wsc<128, true>;
-    const size_t smem = (size_t)gpc * (ctas - 1) * nwords * 8;  // one slot per producer group
-    // the static arrays (up to 40 KB at L = 128) and the ring together may
-    // pass the 48 KB that need no opt-in
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(ctas);
-    cfg.blockDim = dim3(kTinyWsBlock);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr{};
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = ctas;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
+    switch (a.L) {
+    case 64: return launch_wsc<64, true>(a, ctas, s);
+    case 128: return launch_wsc<128, true>(a, ctas, s);
+    case 256: return launch_wsc<256, true>(a, ctas, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tiny(const TinyRunArgs &a, uint32_t block, uint32_t threads_per_word, uint32_t ctas,
                         cudaStream_t s)
 {
     if (!tiny_lattice_ok(a.L) || a.nsweeps == 0) return cudaErrorInvalidValue;
-    if ((a.L == 64 || a.L == 128) && block == kTinyWsBlock && threads_per_word == 1) {
+    if ((a.L == 64 || a.L == 128 || a.L == 256) && block == kTinyWsBlock && threads_per_word == 1) {
         if (!a.use_field) return launch_tiny_ws(a, ctas, s);
         block = kTinyMaxThreads;  // in a field: the field kernels (no warp-specialised form)
     }

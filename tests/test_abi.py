@@ -132,10 +132,10 @@ def test_launch_candidates_are_listed_without_a_gpu(ising):
     assert all(32768 % x["rows_per_item"] == 0 for x in c)
     assert len(ising.ising_launch_candidates(192)) >= 162
     # the one-CTA kernel is a candidate exactly for power-of-two L <= 1024, its
-    # warp-specialised forms (block 1024) at L = 64 (grid 1, 2, 4, 8) and 128
-    # (grid 2, 4, 8)
-    for L, k, ws in ((64, 40, 4), (128, 39, 3), (256, 36, 0), (1024, 36, 0), (192, 0, 0), (2048, 0, 0),
-                     (32768, 0, 0)):
+    # warp-specialised forms (block 1024) at L = 64 (grid 1, 2, 4, 8), 128 and
+    # 256 (grid 2, 4, 8)
+    for L, k, ws in ((64, 40, 4), (128, 39, 3), (256, 39, 3), (512, 36, 0), (1024, 36, 0), (192, 0, 0),
+                     (2048, 0, 0), (32768, 0, 0)):
         tiny = [x for x in ising.ising_launch_candidates(L) if x["proc_bits"] == 8]
         assert len(tiny) == k and sum(x["block"] == 1024 for x in tiny) == ws, L
     # L = 2^20: configurations whose item count does not fit 32 bits are left out

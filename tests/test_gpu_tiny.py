@@ -171,7 +171,7 @@ def test_tiny_cluster_bit_exact(P, orc, L, ctas, tpw):
     lat.close()
 
 
-WS_SHAPES = [(64, 1), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4), (128, 8)]
+WS_SHAPES = [(64, 1), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4), (128, 8), (256, 2), (256, 4), (256, 8)]
 
 
 @pytest.mark.parametrize("L,ctas", WS_SHAPES)
@@ -200,7 +200,8 @@ def test_warp_specialised_is_bit_exact(P, orc, L, ctas):
     lat.close()
 
 
-@pytest.mark.parametrize("L,ctas,hold", [(64, 1, 6), (64, 4, 6), (128, 8, 6), (64, 1, 20), (64, 4, 20), (128, 8, 20)])
+@pytest.mark.parametrize("L,ctas,hold", [(64, 1, 6), (64, 4, 6), (128, 8, 6), (256, 8, 6), (64, 1, 20), (64, 4, 20),
+                                         (128, 8, 20), (256, 8, 20)])
 def test_warp_specialised_wait_runs_out_and_reports(P, monkeypatch, L, ctas, hold):
     """A step whose masks are never announced (a middle step, or the last of
     the call's 20): the consumers' bounded wait runs out, the call reports
@@ -222,7 +223,7 @@ def test_warp_specialised_wait_runs_out_and_reports(P, monkeypatch, L, ctas, hol
     ok.close()
 
 
-@pytest.mark.parametrize("L,ctas", [(64, 1), (128, 4)])
+@pytest.mark.parametrize("L,ctas", [(64, 1), (128, 4), (256, 8)])
 def test_warp_specialised_configuration_in_a_field_runs_the_field_kernel(P, orc, L, ctas):
     """The warp-specialised configuration has no field form: in a field the
     one-CTA or cluster field kernel runs instead, bit-exact with the oracle."""
