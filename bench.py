@@ -97,6 +97,39 @@ def spawn_ranks(n: int) -> int:
 
 
 # ------------------------------------------------------------------ clocks --
+def gpu_local_cpus(gpu_index: int):
+    """The CPUs next to a GPU (sysfs local_cpulist of its PCI device), or None."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        path = "/sys/bus/pci/devices/%04x:%s/local_cpulist" % (int(dom, 16) & 0xFFFF, rest.lower())
+        with open(path) as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
+def compact_cpus(cpus) -> str:
+    out, run = [], []
+    for c in sorted(cpus):
+        if run and c == run[-1] + 1:
+            run.append(c)
+        else:
+            if run:
+                out.append("%d-%d" % (run[0], run[-1]) if len(run) > 1 else str(run[0]))
+            run = [c]
+    if run:
+        out.append("%d-%d" % (run[0], run[-1]) if len(run) > 1 else str(run[0]))
+    return ",".join(out)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -409,7 +442,8 @@ def extras(P, stream, peaks, mix):
         return time.perf_counter() - t
 
     # small lattices: one CTA (L = 64) and an 8-CTA cluster (L = 256)
-    for Ls, name in ((64, "L64_1000_sweeps"), (256, "L256_1000_sweeps")):
+    for Ls in (64, 128, 256, 512):
+        name = "L%d_1000_sweeps" % Ls
         a = P.Lattice(Ls, 2.269185, seed=1, init="cold_up")
         ta = min(wall_call(a, 1000) for _ in range(3))
         n = Ls * Ls * 1000
@@ -421,6 +455,12 @@ def extras(P, stream, peaks, mix):
         d["step_launches_attempts_per_ns"] = n / wall_call(s, 1000) / 1e9
         ctas = max(1, a.launch["grid"])
         d["issue_bound_attempts_per_ns"] = ctas * INT32_LANES_PER_SM * peaks["sm_max_ghz"] / OPS_PER_ATTEMPT
+        # the SMs that draw the acceptance masks (the warp-specialised form
+        # draws in all CTAs but the first) at the measured per-SM draw rate
+        drawing = ctas - 1 if a.launch["block"] == 1024 and ctas > 1 else ctas
+        d["draw_bound_attempts_per_ns"] = drawing * mix["kernel_form_with_masks"] / torch.cuda.get_device_properties(
+            torch.cuda.current_device()).multi_processor_count
+        d["frac_of_draw_bound"] = d["attempts_per_ns"] / d["draw_bound_attempts_per_ns"]
         out[name] = d
         a.close()
         s.close()
@@ -568,9 +608,20 @@ def run_ours(args, ws, rank, local):
     # ---------------- end to end through the C ABI from pinned host memory
     nbytes = N // 8
     e2e_value, h2d, d2h = None, 0, 0
+    local_cpus_used, raw_h2d_gbs = None, None
     if not strips:
-        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-        host.fill_(0xFF)                                  # the cold start, packed
+        # the pinned buffer on the CPU socket next to this GPU (its pages are
+        # placed where they are first touched): bind to the GPU's local CPUs
+        # while allocating and filling it, then restore the affinity
+        local_cpus_used = gpu_local_cpus(local)
+        saved = os.sched_getaffinity(0)
+        if local_cpus_used:
+            os.sched_setaffinity(0, local_cpus_used)
+        try:
+            host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+            host.fill_(0xFF)                              # the cold start, packed
+        finally:
+            os.sched_setaffinity(0, saved)
         hp = host.numpy().view(np.uint64).reshape(L, L // 64)
         Mh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
         Eh = np.zeros(SWEEPS_PER_STEP, dtype=np.int64)
@@ -591,6 +642,16 @@ def run_ours(args, ws, rank, local):
         # the library's device memory from PyTorch's caching allocator, as a
         # caller that runs job after job would set it up: the 32 GiB lattice is
         # allocated once, not cudaMalloc'd and freed in every step
+        # the bare copy from this buffer (torch, outside the timed region): the
+        # reference for the upload phase below
+        dev_probe = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        tc = time.perf_counter()
+        dev_probe.copy_(host, non_blocking=True)
+        torch.cuda.synchronize()
+        raw_h2d_gbs = nbytes / (time.perf_counter() - tc) / 1e9
+        del dev_probe
+        torch.cuda.empty_cache()
         P.use_torch_allocator()
         e2e_clocks = ClockSampler(local)
         try:
@@ -672,7 +733,9 @@ def run_ours(args, ws, rank, local):
                  "how": "per step: ising_create from the pinned packed cold start (H2D), ising_sweep of 10 "
                         "sweeps returning the 10 M/E samples (D2H), ising_destroy; device memory from PyTorch's "
                         "caching allocator (ising_set_allocator)",
-                 "phases_median": e2e_phases, "clocks": e2e_clk}
+                 "phases_median": e2e_phases, "clocks": e2e_clk, "raw_h2d_GBs": raw_h2d_gbs,
+                 "host_buffer_cpus": "the GPU's local CPUs %s" % compact_cpus(local_cpus_used)
+                 if local_cpus_used else "not bound (no local CPU list found)"}
                 if e2e_value is not None else None),
         "gpu_launches": launches,
         "launch": dict(tuned, autotune_us_per_step=tuned_us) if tuned else None,

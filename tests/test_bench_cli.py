@@ -32,3 +32,32 @@ def test_spawn_command_line(monkeypatch):
     assert cmd[cmd.index("--nproc-per-node") + 1] == "4"
     assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
     assert cmd[-4:] == ["--gpus", "4", "--parallelism", "strips"]
+
+
+def test_cpu_list_helpers(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.compact_cpus({0, 1, 2, 3, 8, 10, 11}) == "0-3,8,10-11"
+    assert bench.compact_cpus(set()) == ""
+
+    # a GPU whose PCI device lists CPUs 2-3: the helper returns them (within
+    # the process's own affinity); anything missing gives None
+    class R:
+        stdout = "00000009:01:00.0\n"
+
+    monkeypatch.setattr(bench.subprocess, "run", lambda *a, **k: R())
+    real_open = open
+
+    def fake_open(path, *a, **k):
+        if path == "/sys/bus/pci/devices/0009:01:00.0/local_cpulist":
+            import io
+            return io.StringIO("2-3\n")
+        return real_open(path, *a, **k)
+
+    monkeypatch.setattr("builtins.open", fake_open)
+    mine = os.sched_getaffinity(0)
+    got = bench.gpu_local_cpus(0)
+    assert got == ({2, 3} & mine or None)
+    monkeypatch.setattr("builtins.open", real_open)
+    assert bench.gpu_local_cpus(0) is None
