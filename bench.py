@@ -258,6 +258,64 @@ def oracle_one_core(target_s: float, rows: int = 64):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def oracle_configs(one_thread: bool = False) -> dict:
+    """The oracle on the other workloads (bounded samples, each a few seconds
+    at most): the L = 64 case in full (1000 sweeps, one thread), the L = 32768
+    case (two whole-lattice sweeps on all cores; a 10-sweep light-cone window of
+    256 rows on one thread) and one lattice per size of the 128-lattice batch
+    (200 sweeps each, all cores).  With one_thread, only the one-thread parts."""
+    import numpy as np
+
+    import oracle
+    from paper_1007_3726_gb300 import workloads as WL
+
+    oracle.build()
+    out = {}
+    if one_thread:
+        thr4, thr8 = oracle.thresholds(2.269185)
+        s = oracle.init_cold(64)
+        t = time.perf_counter()
+        oracle.run(s, 1000, 1, 0, thr4, thr8, check=False)
+        el = time.perf_counter() - t
+        out["L64_1000_sweeps_1_thread"] = {"value": 64 * 64 * 1000 / el / 1e9, "seconds": el}
+        w = WL.large_L32768()
+        thr4, thr8 = oracle.thresholds(w["T"])
+        s = oracle.init_hot(w["L"], w["seed"], w["stream_id"], 0, 256)
+        t = time.perf_counter()
+        oracle.run_window(s, w["L"], 0, 10, w["seed"], w["stream_id"], thr4, thr8)
+        el = time.perf_counter() - t
+        out["L32768_window_1_thread"] = {"value": 254 * w["L"] * 10 / el / 1e9, "seconds": el,
+                                         "sample": "rows 0-255, 10 sweeps (light-cone mode)"}
+        return out
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    w = WL.large_L32768()
+    thr4, thr8 = oracle.thresholds(w["T"])
+    s = oracle.init_hot(w["L"], w["seed"], w["stream_id"])
+    t = time.perf_counter()
+    oracle.run(s, 2, w["seed"], w["stream_id"], thr4, thr8, check=False)
+    el = time.perf_counter() - t
+    out["L32768_2_sweeps"] = {"value": w["L"] ** 2 * 2 / el / 1e9, "seconds": el, "cores": threads}
+    del s
+    attempts, el = 0, 0.0
+    for sp in WL.fss_batch()[::32]:  # the first temperature of each size
+        thr4, thr8 = oracle.thresholds(sp["T"])
+        s = oracle.init_hot(sp["L"], sp["seed"], sp["stream_id"])
+        t = time.perf_counter()
+        oracle.run(s, 200, sp["seed"], sp["stream_id"], thr4, thr8, check=False)
+        el += time.perf_counter() - t
+        attempts += sp["L"] ** 2 * 200
+    out["fss_one_lattice_per_L_200_sweeps"] = {"value": attempts / el / 1e9, "seconds": el, "cores": threads}
+    return out
+
+
+def oracle_configs_one_thread() -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = "import json, bench; print(json.dumps(bench.oracle_configs(one_thread=True)))"
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def msc_sample(target_s: float):
     """The paper's CPU multi-spin-coding program (Sec. 4, a Boltzmann-pattern pool
     of 2^22 entries) on its Table 1 shape, L = 4096 at T = 0.99 T_c, hot start:
@@ -301,7 +359,9 @@ def cpu_baseline(target_s=10.0):
            "all_cores": {"value": m / elm / 1e9, "cores": thrm, "sweeps": swm, "seconds": elm},
            "one_core": {"value": m1 / elm1 / 1e9, "cores": thrm1, "sweeps": swm1, "seconds": elm1},
            "paper_one_core": {"value": 0.2267, "hardware": "Intel Xeon X5560 2.80 GHz, 1 core (Table 1)"}}
+    per_config = dict(oracle_configs(), **oracle_configs_one_thread())
     return {"value": a / el / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle", "paper_cpu_msc": msc,
+            "per_config": dict(per_config, unit=UNIT),
             "sample": "oracle (one int8 per spin, plain C, OpenMP over rows) on rows 0-255 of the "
                       "L=524288 cold start, %d sweeps in light-cone mode, %.1f s wall, %d threads"
                       % (sw, el, thr),
