@@ -238,14 +238,15 @@ ISING_API const char *ising_last_error(void);
  * the default for L <= 512 (the warp-specialised cluster form below at L = 64,
  * 128 and 256, a cluster of 8 at 512).  At L = 64, 128 and 256, block 1024 with
  * one thread per word selects the warp-specialised form: consumer threads keep
- * the lattice in registers and update it (one word each, at L = 256 a vertical
- * run of four), producer groups draw the acceptance masks of later steps into
- * a ring of tagged entries in the consumers' shared memory, and mbarriers hand
- * the ring slots back.  With grid 1 (L = 64 only) producers and consumers share
- * one CTA; with grid 2, 4 or 8 the first CTA of a cluster holds the consumers
- * and the other CTAs the producers, which store through distributed shared
- * memory.  Every wait is bounded: when one runs out
- * the call returns ISING_ERR_TIMEOUT and the handle is failed (the environment
+ * the lattice in registers and update it (one word each at L = 64, a vertical
+ * run of two or four words at L = 128 and 256), producer groups draw the
+ * acceptance masks of later steps into a ring of tagged entries in the
+ * consumers' shared memory, and mbarriers hand the ring slots back.  With grid
+ * 1 (L = 64 only) producers and consumers share one CTA; with grid 2, 4 or 8
+ * the first CTA of a cluster holds the consumers and the other CTAs the
+ * producers, which store through distributed shared memory.  Every wait is
+ * bounded: when one runs out the call returns ISING_ERR_TIMEOUT and the handle
+ * is failed (the environment
  * variable ISING_TINY_HOLD_STEP = 1 + a step index withholds that step's
  * masks, for failure-detection tests only).  In a field (H != 0) it uses one
  * thread per word whatever rows_per_item says, and the warp-specialised

@@ -261,8 +261,8 @@ __global__ void __launch_bounds__(kTinyMaxThreads) k_tiny(const __grid_constant_
 // barrier of each step are short, the Philox draws long.  The draws do not
 // depend on the spins, so the roles are split:
 //   consumers  threads of the first CTA that keep the lattice in registers:
-//              one word each, or at L = 256 a vertical run of four words of
-//              one column.  The left and right neighbour words come from other
+//              one word each at L = 64, at L = 128 and 256 a vertical run of two
+//              and four words of one column.  The left and right neighbour words come from other
 //              lanes by warp shuffles, so do the rows above and below a run,
 //              and the rows across a warp boundary through a small shared
 //              array.  A step is the ring entries, the bit logic, one store of
@@ -446,7 +446,7 @@ template <uint32_t LL, bool CL>
 struct WsShape {
     static constexpr uint32_t W = LL / 32;                  // words per row
     static constexpr uint32_t NWORDS = LL * W;              // words of the lattice
-    static constexpr uint32_t WPT = LL >= 256 ? NWORDS / 512 : 1;  // words per consumer thread
+    static constexpr uint32_t WPT = LL >= 256 ? NWORDS / 512 : LL == 128 ? 2 : 1;  // words per consumer thread
     static constexpr uint32_t NCONS = NWORDS / WPT;         // consumer threads
     static constexpr uint32_t NCW = NCONS / 32;             // consumer warps
     static constexpr uint32_t GT = NWORDS < kTinyWsBlock ? NWORDS : kTinyWsBlock;  // threads of a producer group
