@@ -246,9 +246,10 @@ ISING_API const char *ising_last_error(void);
  * the first CTA of a cluster holds the consumers and the other CTAs the
  * producers, which store through distributed shared memory.  Every wait is
  * bounded: when one runs out the call returns ISING_ERR_TIMEOUT and the handle
- * is failed (the environment
- * variable ISING_TINY_HOLD_STEP = 1 + a step index withholds that step's
- * masks, for failure-detection tests only).  In a field (H != 0) it uses one
+ * is failed (the environment variable ISING_TINY_HOLD_STEP = 1 + a step index
+ * withholds that step's masks, for failure-detection tests only).  A call of
+ * more than 2^30 sweeps runs as several launches of at most 2^30 sweeps each
+ * (ISING_TINY_MAX_SWEEPS lowers that bound, for tests only).  In a field (H != 0) it uses one
  * thread per word whatever rows_per_item says, and the warp-specialised
  * configurations run the one-CTA or cluster field kernel with block 512; the
  * step kernels are then replaced by the field step kernel.

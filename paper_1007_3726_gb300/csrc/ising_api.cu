@@ -442,7 +442,30 @@ ising_status ising_sweep(ising_lattice *h, uint64_t nsweeps, uint32_t record_eve
             const char *hold = std::getenv("ISING_TINY_HOLD_STEP");
             ta.hold_step = hold ? (uint32_t)std::strtoul(hold, nullptr, 10) : 0u;
         }
-        CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->launch.grid, h->stream));
+        // A launch counts its checkerboard steps (2 per sweep) in 32 bits: a
+        // longer call runs as several launches of at most 2^30 sweeps.  Launch k
+        // records its samples from slot rec_done on; its final-state slot is the
+        // next launch's first sample slot, cleared in between (some of these
+        // kernels add their counts into the slots).
+        uint64_t max_chunk = 1ull << 30;
+        if (const char *mx = std::getenv("ISING_TINY_MAX_SWEEPS")) {  // testing only
+            const uint64_t v = std::strtoull(mx, nullptr, 10);
+            if (v > 0 && v < max_chunk) max_chunk = v;
+        }
+        uint64_t done = 0, rec_done = 0;
+        while (done < nsweeps) {
+            const uint64_t n = std::min(nsweeps - done, max_chunk);
+            const uint64_t tc = t0 + done;
+            const uint64_t nrec_c = record_every ? (tc + n) / record_every - tc / record_every : 0;
+            if (done > 0) CK(h, cudaMemsetAsync(h->d_acc + 2 * rec_done, 0, 16, h->stream));
+            ta.t0 = (uint32_t)tc;
+            ta.nsweeps = (uint32_t)n;
+            ta.nrec = (uint32_t)nrec_c;
+            ta.acc = h->d_acc + 2 * rec_done;
+            CK(h, launch_tiny(ta, h->launch.block, h->launch.rows_per_item, h->launch.grid, h->stream));
+            done += n;
+            rec_done += nrec_c;
+        }
         h->pending_err = true;
         return finish_sweep_call(h, t0, nsweeps, nrec, M_out, E_out);
     }

@@ -16,6 +16,7 @@
 #include "runtime.h"
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -142,7 +143,28 @@ extern "C" ISING_API ising_status ising_sweep_noalloc(void *d_spins, uint64_t L,
         // the slot after it is the error flag of the one-CTA kernels
         ta.err = reinterpret_cast<unsigned int *>(acc + 2 * (nrec + 1));
         e = cudaMemsetAsync(acc, 0, (nrec + 2) * 2 * sizeof(unsigned long long), s);
-        if (e == cudaSuccess) e = launch_tiny(ta, dflt.block, dflt.rows_per_item, dflt.grid, s);
+        // launches of at most 2^30 sweeps (a launch counts its steps in 32 bits),
+        // as in ising_sweep: launch k records from slot rec_done on, and its
+        // final-state slot, the next launch's first sample slot, is cleared
+        uint64_t max_chunk = 1ull << 30;
+        if (const char *mx = std::getenv("ISING_TINY_MAX_SWEEPS")) {  // testing only
+            const uint64_t v = std::strtoull(mx, nullptr, 10);
+            if (v > 0 && v < max_chunk) max_chunk = v;
+        }
+        uint64_t done = 0, rec_done = 0;
+        while (e == cudaSuccess && done < nsweeps) {
+            const uint64_t n = nsweeps - done < max_chunk ? nsweeps - done : max_chunk;
+            const uint64_t tc = t0 + done;
+            const uint64_t nrec_c = record_every ? (tc + n) / record_every - tc / record_every : 0;
+            if (done > 0) e = cudaMemsetAsync(acc + 2 * rec_done, 0, 2 * sizeof(unsigned long long), s);
+            ta.t0 = (uint32_t)tc;
+            ta.nsweeps = (uint32_t)n;
+            ta.nrec = (uint32_t)nrec_c;
+            ta.acc = acc + 2 * rec_done;
+            if (e == cudaSuccess) e = launch_tiny(ta, dflt.block, dflt.rows_per_item, dflt.grid, s);
+            done += n;
+            rec_done += nrec_c;
+        }
     }
     const LaunchConfig cfg = plain_launch(dflt);
     uint64_t slot = 0;

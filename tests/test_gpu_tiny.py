@@ -236,3 +236,44 @@ def test_warp_specialised_configuration_in_a_field_runs_the_field_kernel(P, orc,
     assert np.array_equal(M, Mo) and np.array_equal(E, Eo)
     assert np.array_equal(lat.spins(), s)
     lat.close()
+
+
+@pytest.mark.parametrize("L,launch", [(64, None), (128, None), (256, None), (512, None),
+                                      (64, dict(TINY, block=1024, rows_per_item=1, grid=1)),
+                                      (128, dict(TINY, block=256, rows_per_item=2))])
+def test_long_calls_run_as_several_launches(P, orc, monkeypatch, L, launch):
+    """A call longer than one launch's sweep bound runs as several launches
+    (forced here with a bound of 7 sweeps): the lattice and every sample equal
+    the oracle's, with samples spread over the launches and a final state slot
+    that each launch hands to the next."""
+    T, seed, sid = 2.269185, 23, 2
+    thr4, thr8 = orc.thresholds(T)
+    lat = P.Lattice(L, T, seed=seed, stream_id=sid, init="hot")
+    if launch is not None:
+        lat.set_launch(**launch)
+    monkeypatch.setenv("ISING_TINY_MAX_SWEEPS", "7")
+    s = orc.init_hot(L, seed, sid)
+    t = 0
+    for n, rec in ((50, 3), (15, 0), (22, 1)):
+        got = lat.sweep(n, rec, collect=bool(rec))
+        Mo, Eo = orc.run(s, n, seed, sid, thr4, thr8, t0=t)
+        if rec:
+            k0 = (rec - 1 - t) % rec
+            assert np.array_equal(got[0], Mo[k0::rec]) and np.array_equal(got[1], Eo[k0::rec]), (n, rec)
+        d = lat.measure()
+        assert (d["M"], d["E"]) == (Mo[-1], Eo[-1])
+        t += n
+    assert np.array_equal(lat.spins(), s)
+    lat.close()
+
+
+def test_long_calls_in_a_field_run_as_several_launches(P, orc, monkeypatch):
+    L, T, H, seed = 64, 2.1, 0.3, 9
+    lat = P.Lattice(L, T, seed=seed, init="hot", H=H)
+    monkeypatch.setenv("ISING_TINY_MAX_SWEEPS", "5")
+    M, E = lat.sweep(23, 2, collect=True)
+    s = orc.init_hot(L, seed, 0)
+    Mo, Eo = orc.run_field(s, 23, seed, 0, T, H)
+    assert np.array_equal(M, Mo[1::2]) and np.array_equal(E, Eo[1::2])
+    assert np.array_equal(lat.spins(), s)
+    lat.close()

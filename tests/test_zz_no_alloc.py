@@ -48,6 +48,30 @@ def test_noalloc_matches_ising_sweep_on_two_calls(P, L, word_bits, record_every)
     ref.close()
 
 
+@pytest.mark.parametrize("L", [64, 256, 512])
+def test_noalloc_long_calls_run_as_several_launches(P, monkeypatch, L):
+    """The small-lattice kernels take at most 2^30 sweeps per launch (forced
+    down to 6 here): the samples spread over the launches and the state after
+    the call equal ising_sweep's."""
+    import torch
+
+    T, seed, stream_id = 2.269185, 41, 3
+    ref = P.Lattice(L, T, seed=seed, stream_id=stream_id, init="hot", word_bits=32)
+    packed = ref.packed()
+    dev = torch.from_numpy(packed.view(np.int64).copy()).cuda()
+    torch.cuda.synchronize()
+    Mr, Er = ref.sweep(40, 3, collect=True)
+    k = 40 // 3
+    M = np.zeros(k, dtype=np.int64)
+    E = np.zeros(k, dtype=np.int64)
+    monkeypatch.setenv("ISING_TINY_MAX_SWEEPS", "6")
+    P.ising_sweep_noalloc(dev.data_ptr(), L, 32, T, seed, stream_id, 0, 40, 3, M, E, k)
+    assert np.array_equal(M, Mr) and np.array_equal(E, Er)
+    got = dev.cpu().numpy().view(packed.dtype).reshape(packed.shape)
+    assert np.array_equal(got, ref.packed())
+    ref.close()
+
+
 def test_noalloc_rejects_more_samples_than_its_scratch(P):
     import torch
 
